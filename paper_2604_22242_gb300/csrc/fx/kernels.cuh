@@ -1,0 +1,808 @@
+// kernels.cuh - the fused sm_103a kernels (one kernel per expression tree).
+//
+// Every kernel works in two phases per step: first it issues the loads of
+// every distinct leaf for all of its vectors (register packs, so many
+// independent 16/32-byte loads are in flight per thread), then it evaluates
+// the tree lane by lane from registers and hands the results to an
+// epilogue (store, fused reduction, or both). Intermediate values of the
+// tree never leave registers: each input element is read once and each
+// output element written once (Sec. 5: one pass over the input matrices).
+//
+// Reductions are deterministic: each thread accumulates a compensated
+// (s, c) pair over a fixed set of elements; warps and blocks combine pairs
+// in a fixed butterfly order; each block writes one partial; the last block
+// to finish (an atomic ticket, no waiting) sums the partials in a fixed
+// order in FP64 and writes the result. No block ever waits on another.
+#pragma once
+
+#include "plan.cuh"
+
+namespace fx {
+
+// ---------------------------------------------------------------- launch data
+
+struct SlotView {
+  const void* p;
+  int64_t ld;  // leading dimension (matrix leaves)
+  int64_t vs;  // element stride of a vector leaf: 1 (rows x 1) or ld (1 x cols)
+};
+struct Slots {
+  SlotView s[FX_MAX_SLOTS];
+};
+
+// Reduction workspace: per-block partials and the completion ticket.
+struct RedArgs {
+  double2* part;
+  unsigned int* ticket;
+  void* out;  // float* or double* (the reduction type)
+};
+
+// ---------------------------------------------------------------- register packs
+
+template <class L, int V, class CT> struct pack_elem {
+  using T = typename L::elem;
+  using type = std::conditional_t<L::mode == MT, Raw<CT, V>, Raw<T, (L::mode == MBR ? 1 : V)>>;
+};
+
+template <class LL, int V, class CT> struct Pack;
+template <int V, class CT> struct Pack<TL<>, V, CT> {};
+template <class H, class... Ts, int V, class CT> struct Pack<TL<H, Ts...>, V, CT> {
+  typename pack_elem<H, V, CT>::type h;
+  Pack<TL<Ts...>, V, CT> t;
+};
+
+template <int I> struct pget {
+  template <class P> static FX_D auto& of(P& p) { return pget<I - 1>::of(p.t); }
+};
+template <> struct pget<0> {
+  template <class P> static FX_D auto& of(P& p) { return p.h; }
+};
+
+// Element context: lane j of a pack.
+template <class LL, int V, class CTy> struct Ctx {
+  using CT = CTy;
+  const Pack<LL, V, CT>& p;
+  int j;
+  template <int K, int M> FX_D CT leaf() const {
+    constexpr int I = tl_index<LL, K, M>::value;
+    static_assert(I >= 0, "leaf not in the pack");
+    const auto& r = pget<I>::of(p);
+    if constexpr (M == MT) {
+      return r.v[j];
+    } else if constexpr (M == MBR) {
+      return to_compute<CT>(r.v[0]);
+    } else {
+      return to_compute<CT>(r.v[j]);
+    }
+  }
+};
+
+template <int V, class E, class LL, class CT>
+FX_D void eval_lanes(const E& e, const Pack<LL, V, CT>& p, CT (&v)[V]) {
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    Ctx<LL, V, CT> c{p, j};
+    v[j] = e.ev(c);
+  }
+}
+
+FX_D int clamp_valid(int64_t left, int V) {
+  return left >= V ? V : (left > 0 ? int(left) : 0);
+}
+
+// ---------------------------------------------------------------- leaf loads
+
+// Flat layout (all leaves MN and contiguous): element i of every leaf.
+template <class LL, int V, class CT, int I = 0>
+FX_D void load_flat(Pack<LL, V, CT>& p, const Slots& sl, int64_t i) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    static_assert(L::mode == MN, "flat kernels take plain leaves only");
+    vload(pget<I>::of(p), static_cast<const T*>(sl.s[L::slot].p) + i);
+    load_flat<LL, V, CT, I + 1>(p, sl, i);
+  }
+}
+
+// Column-vector layout: rows r .. r+V-1 (nvalid of them inside the
+// matrix) of column c. V > 1 means the host checked that every such full
+// vector is aligned for one access. MT leaves are filled from shared memory
+// by the tiled kernel, not here.
+template <class LL, int V, class CT, int I = 0>
+FX_D void load_rc(Pack<LL, V, CT>& p, const Slots& sl, int64_t r, int64_t c, int nvalid) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    auto& dst = pget<I>::of(p);
+    const SlotView& s = sl.s[L::slot];
+    const T* base = static_cast<const T*>(s.p);
+    if constexpr (L::mode == MN) {
+      const T* q = base + r + c * s.ld;
+      if (nvalid == V) {
+        vload(dst, q);
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) dst.v[j] = j < nvalid ? sload(q + j) : T(0.0f);
+      }
+    } else if constexpr (L::mode == MBC) {
+      const T* q = base + r * s.vs;
+      if (nvalid == V && s.vs == 1) {
+        vload(dst, q);
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) dst.v[j] = j < nvalid ? sload(q + j * s.vs) : T(0.0f);
+      }
+    } else if constexpr (L::mode == MBR) {
+      dst.v[0] = sload(base + c * s.vs);
+    }
+    load_rc<LL, V, CT, I + 1>(p, sl, r, c, nvalid);
+  }
+}
+
+// ---------------------------------------------------------------- epilogues
+//
+// put(state, off, v, nvalid): lanes 0..nvalid-1 of v are the tree's values
+// at output offset off .. off+nvalid-1 (off = r + c*ldz).
+
+template <class T, int V> struct EpiStore {
+  T* z;
+  int64_t ldz;
+  static constexpr bool reduces = false;
+  static constexpr bool sqrt_result = false;
+  struct State {
+    FX_D void init() {}
+  };
+  template <class CT> FX_D void put(State&, int64_t off, const CT (&v)[V], int nvalid) const {
+    if (nvalid == V) {
+      Raw<T, V> o;
+#pragma unroll
+      for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(v[j]);
+      vstore(z + off, o);
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid) sstore(z + off + j, narrow_to<T>::from(v[j]));
+    }
+  }
+};
+
+// Fused sum of the elements (SQ: of their squares, for the 2-norm).
+template <class CTy, int V, bool SQ> struct EpiSum {
+  int64_t ldz;
+  static constexpr bool reduces = true;
+  static constexpr bool sqrt_result = SQ;
+  using State = ThreadSum<CTy>;
+  template <class CT> FX_D void put(State& st, int64_t, const CT (&v)[V], int nvalid) const {
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      if (j < nvalid) st.add(SQ ? v[j] * v[j] : v[j]);
+  }
+};
+
+// Store and sum (a tree with an accu side output: Z and accu(Z)).
+template <class T, int V> struct EpiStoreSum {
+  T* z;
+  int64_t ldz;
+  static constexpr bool reduces = true;
+  static constexpr bool sqrt_result = false;
+  using State = ThreadSum<compute_t<T>>;
+  template <class CT> FX_D void put(State& st, int64_t off, const CT (&v)[V], int nvalid) const {
+    EpiStore<T, V> s{z, ldz};
+    typename EpiStore<T, V>::State d;
+    s.put(d, off, v, nvalid);
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      if (j < nvalid) st.add(v[j]);
+  }
+};
+
+// ---------------------------------------------------------------- combines
+
+template <class S> FX_D void warp_merge(S& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    auto s2 = __shfl_xor_sync(0xffffffffu, a.s, o);
+    auto c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+    a.merge(s2, c2);
+  }
+}
+
+// Block-wide merge of per-thread pairs; the total is valid in thread 0.
+// Fixed order: butterfly in each warp, then warp 0 over the warp totals.
+template <class S> FX_D void block_merge(S& a) {
+  using CT = decltype(a.s);
+  __shared__ CT bs[32], bc[32];
+  warp_merge(a);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();  // bs/bc may still be read by a previous call
+  if (lane == 0) {
+    bs[w] = a.s;
+    bc[w] = a.c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a.s = lane < nw ? bs[lane] : CT(0);
+    a.c = lane < nw ? bc[lane] : CT(0);
+    warp_merge(a);
+  }
+}
+
+template <class CT> FX_D CT warp_max(CT m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
+}
+template <class CT> FX_D CT block_max(CT m) {
+  __shared__ CT bm[32];
+  m = warp_max(m);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) bm[w] = m;
+  __syncthreads();
+  if (w == 0) m = warp_max(lane < nw ? bm[lane] : neg_inf<CT>());
+  return m;
+}
+
+// Fixed-order FP64 compensated sum of n partial pairs part[i*stride]; the
+// result is valid in thread 0. Every thread of the block must call it.
+FX_D double block_sum_partials(const double2* part, int64_t n, int64_t stride) {
+  CompSum<double> a;
+  a.init();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double2 q = __ldcg(part + i * stride);
+    a.add(q.x);
+    a.add(q.y);
+  }
+  block_merge(a);
+  return a.s + a.c;
+}
+
+// Every block publishes its partial; the last one combines all of them.
+template <class CT, bool SQRT, class S> FX_D void finish_full_reduce(S& a, const RedArgs& red) {
+  block_merge(a);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    red.part[blockIdx.x] = make_double2(double(a.s), double(a.c));
+    __threadfence();
+    unsigned int t = atomicAdd(red.ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot = block_sum_partials(red.part, gridDim.x, 1);
+  if (threadIdx.x == 0) {
+    if (SQRT) tot = ::sqrt(tot);
+    *static_cast<CT*>(red.out) = static_cast<CT>(tot);
+    *red.ticket = 0u;  // ready for the next launch on this stream
+  }
+}
+
+// ---------------------------------------------------------------- A3: flat stream
+
+template <class E, class Epi, int V, int U>
+__global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const int64_t n,
+                                              const Epi epi, const RedArgs red) {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  const int64_t nv = n / V;
+  const int64_t bdim = blockDim.x;
+  const int64_t step = int64_t(gridDim.x) * bdim * U;
+  typename Epi::State st;
+  st.init();
+  for (int64_t b = int64_t(blockIdx.x) * bdim * U + threadIdx.x; b < nv; b += step) {
+    Pack<LL, V, CT> p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t vi = b + u * bdim;
+      if (vi < nv) load_flat(p[u], sl, vi * V);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t vi = b + u * bdim;
+      if (vi < nv) {
+        CT v[V];
+        eval_lanes<V>(e, p[u], v);
+        epi.put(st, vi * V, v, V);
+      }
+    }
+  }
+  if (V > 1 && blockIdx.x == 0) {  // the n % V trailing elements, one lane each
+    for (int64_t i = nv * V + threadIdx.x; i < n; i += bdim) {
+      Pack<LL, 1, CT> q;
+      load_flat(q, sl, i);
+      CT v1[1];
+      eval_lanes<1>(e, q, v1);
+      CT v[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) v[j] = v1[0];
+      epi.put(st, i, v, 1);
+    }
+  }
+  if constexpr (Epi::reduces) finish_full_reduce<CT, Epi::sqrt_result>(st, red);
+}
+
+// ---------------------------------------------------------------- A4: tiles
+//
+// A block owns TR x TC output tiles. Thread (tx, ty) handles rows
+// r0 + V*tx .. +V-1 of columns c0 + ty + TY*q, q < P. A transposed leaf D
+// (C x R) is read along its own columns - rows c0 .. c0+TC-1 of D, which
+// are contiguous - with vector loads, staged in shared memory as S[r][c]
+// (row stride TC + 1: odd, so column reads are free of bank conflicts),
+// and read back in output order, so both the load of D and the store of Z
+// stay coalesced (the swapped index of the Sec. 3 transpose rule, used
+// directly, would read D with stride ld).
+
+template <class LL, int I = 0> FX_HD constexpr int count_mt() {
+  if constexpr (I < tl_size<LL>::value) {
+    return (tl_at<LL, I>::type::mode == MT ? 1 : 0) + count_mt<LL, I + 1>();
+  } else {
+    return 0;
+  }
+}
+template <class LL, int I, int J = 0> FX_HD constexpr int mt_rank() {  // index among MT leaves
+  if constexpr (J < I) {
+    return (tl_at<LL, J>::type::mode == MT ? 1 : 0) + mt_rank<LL, I, J + 1>();
+  } else {
+    return 0;
+  }
+}
+
+template <class E, int V_, int TR_, int TC_, int NT_> struct TileShape {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  static constexpr int V = V_, TR = TR_, TC = TC_, NT = NT_;
+  static constexpr int TX = TR / V, TY = NT / TX, P = TC / TY;
+  static_assert(TX * V == TR && TX * TY == NT && P * TY == TC, "bad tile shape");
+  // transposed-leaf staging: vectors along D's rows (the output's columns)
+  static constexpr int DX = TC / V, DY = NT / DX, DP = TR / DY;
+  static_assert(DX * V == TC && DX * DY == NT && DP * DY == TR, "bad staging shape");
+  static constexpr int NMT = count_mt<LL>();
+  static constexpr int SROW = TC + 1;
+  static constexpr int SMEM = (NMT > 0 ? NMT : 1) * TR * SROW;  // elements of CT
+};
+
+// Global loads of the transposed leaves' tiles into registers.
+template <class TS, int I = 0>
+FX_D void mt_fetch(typename TS::CT (&regs)[TS::NMT > 0 ? TS::NMT : 1][TS::DP][TS::V],
+                   const Slots& sl, int64_t R, int64_t C, int64_t r0, int64_t c0) {
+  using LL = typename TS::LL;
+  using CT = typename TS::CT;
+  constexpr int V = TS::V;
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    if constexpr (L::mode == MT) {
+      using T = typename L::elem;
+      constexpr int m = mt_rank<LL, I>();
+      const SlotView& s = sl.s[L::slot];
+      const T* base = static_cast<const T*>(s.p);
+      const int dx = threadIdx.x % TS::DX, dy = threadIdx.x / TS::DX;
+      const int64_t c = c0 + int64_t(dx) * V;  // row of D
+      const int nvalid = clamp_valid(C - c, V);
+#pragma unroll
+      for (int q = 0; q < TS::DP; ++q) {
+        const int64_t r = r0 + dy + int64_t(q) * TS::DY;  // column of D
+        Raw<T, V> w;
+        if (r < R && nvalid > 0) {
+          const T* src = base + c + r * s.ld;
+          if (nvalid == V) {
+            vload(w, src);
+          } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) w.v[j] = j < nvalid ? sload(src + j) : T(0.0f);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < V; ++j) w.v[j] = T(0.0f);
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) regs[m][q][j] = to_compute<CT>(w.v[j]);
+      }
+    }
+    mt_fetch<TS, I + 1>(regs, sl, R, C, r0, c0);
+  }
+}
+
+// Shared-memory values of the transposed leaves for the thread's vectors.
+template <class TS, int I = 0>
+FX_D void mt_fill(Pack<typename TS::LL, TS::V, typename TS::CT> (&p)[TS::P],
+                  const typename TS::CT* sm) {
+  using LL = typename TS::LL;
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    if constexpr (L::mode == MT) {
+      constexpr int m = mt_rank<LL, I>();
+      const int tx = threadIdx.x % TS::TX, ty = threadIdx.x / TS::TX;
+#pragma unroll
+      for (int q = 0; q < TS::P; ++q)
+#pragma unroll
+        for (int j = 0; j < TS::V; ++j)
+          pget<I>::of(p[q]).v[j] =
+              sm[(m * TS::TR + tx * TS::V + j) * TS::SROW + ty + q * TS::TY];
+    }
+    mt_fill<TS, I + 1>(p, sm);
+  }
+}
+
+// One TR x TC tile at (r0, c0) of an R x C tree.
+template <class TS, class E, class Epi>
+FX_D void tile_body(const E& e, const Slots& sl, int64_t R, int64_t C, int64_t r0, int64_t c0,
+                    const Epi& epi, typename Epi::State& st, typename TS::CT* sm) {
+  using LL = typename TS::LL;
+  using CT = typename TS::CT;
+  constexpr int V = TS::V;
+  const int tx = threadIdx.x % TS::TX, ty = threadIdx.x / TS::TX;
+  const int64_t r = r0 + int64_t(tx) * V;
+  const int nvalid = clamp_valid(R - r, V);
+  Pack<LL, V, CT> p[TS::P];
+#pragma unroll
+  for (int q = 0; q < TS::P; ++q) {
+    const int64_t c = c0 + ty + int64_t(q) * TS::TY;
+    if (c < C && nvalid > 0) load_rc(p[q], sl, r, c, nvalid);
+  }
+  if constexpr (TS::NMT > 0) {
+    CT regs[TS::NMT][TS::DP][V];
+    mt_fetch<TS>(regs, sl, R, C, r0, c0);
+    __syncthreads();  // the previous tile's readers are done with sm
+    const int dx = threadIdx.x % TS::DX, dy = threadIdx.x / TS::DX;
+#pragma unroll
+    for (int m = 0; m < TS::NMT; ++m)
+#pragma unroll
+      for (int q = 0; q < TS::DP; ++q)
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          sm[(m * TS::TR + dy + q * TS::DY) * TS::SROW + dx * V + j] = regs[m][q][j];
+    __syncthreads();
+    mt_fill<TS>(p, sm);
+  }
+#pragma unroll
+  for (int q = 0; q < TS::P; ++q) {
+    const int64_t c = c0 + ty + int64_t(q) * TS::TY;
+    if (c < C && nvalid > 0) {
+      CT v[V];
+      eval_lanes<V>(e, p[q], v);
+      epi.put(st, r + c * epi.ldz, v, nvalid);
+    }
+  }
+}
+
+template <class E, class Epi, int V, int TR, int TC, int NT>
+__global__ void __launch_bounds__(NT) k_tile(const E e, const Slots sl, const int64_t R,
+                                             const int64_t C, const Epi epi, const RedArgs red) {
+  using TS = TileShape<E, V, TR, TC, NT>;
+  using CT = typename TS::CT;
+  __shared__ CT sm[TS::SMEM];
+  typename Epi::State st;
+  st.init();
+  const int64_t tiles_r = (R + TR - 1) / TR;
+  const int64_t ntiles = tiles_r * ((C + TC - 1) / TC);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t tr = t % tiles_r, tc = t / tiles_r;
+    tile_body<TS>(e, sl, R, C, tr * TR, tc * TC, epi, st, sm);
+  }
+  if constexpr (Epi::reduces) finish_full_reduce<CT, Epi::sqrt_result>(st, red);
+}
+
+// ---------------------------------------------------------------- A6: dim reductions
+//
+// sum/max along dim 0 (one value per column): columns are contiguous, so
+// a group of G threads (a warp, or the whole block) walks one column with
+// vector loads and reduces in a fixed order. Output (0, c) at out[c*ldo].
+
+template <class E, bool ISMAX, int V, int U, int G, int NT>
+__global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int64_t R,
+                                            const int64_t C, void* out, const int64_t ldo) {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  static_assert(G == 32 || G == NT, "a column is reduced by a warp or a block");
+  constexpr int GPB = NT / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x % G;
+  for (int64_t cb = int64_t(blockIdx.x) * GPB; cb < C; cb += int64_t(gridDim.x) * GPB) {
+    const int64_t c = cb + g;
+    ThreadSum<CT> acc;
+    acc.init();
+    CT m = neg_inf<CT>();
+    if (c < C) {
+      for (int64_t rb = int64_t(lane) * V; rb < R; rb += int64_t(G) * V * U) {
+        Pack<LL, V, CT> p[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t r = rb + int64_t(u) * G * V;
+          const int nv = clamp_valid(R - r, V);
+          if (nv > 0) load_rc(p[u], sl, r, c, nv);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t r = rb + int64_t(u) * G * V;
+          const int nv = clamp_valid(R - r, V);
+          if (nv > 0) {
+            CT v[V];
+            eval_lanes<V>(e, p[u], v);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+              if (j < nv) {
+                if (ISMAX) m = max_nan(m, v[j]);
+                else acc.add(v[j]);
+              }
+            }
+          }
+        }
+      }
+    }
+    CT res;
+    if constexpr (G == 32) {
+      if (ISMAX) {
+        res = warp_max(m);
+      } else {
+        warp_merge(acc);
+        res = CT(double(acc.s) + double(acc.c));
+      }
+    } else {
+      if (ISMAX) {
+        res = block_max(m);
+      } else {
+        block_merge(acc);
+        res = CT(double(acc.s) + double(acc.c));
+      }
+    }
+    if (lane == 0 && c < C) static_cast<CT*>(out)[c * ldo] = res;
+  }
+}
+
+// sum/max along dim 1 (one value per row): rows are strided, so a thread
+// owns V consecutive rows and walks the columns of its split; a warp reads
+// 32*V contiguous elements per column. With S > 1 column splits, each
+// block writes per-row partials and the last of the S blocks of its row
+// range (an atomic ticket per range) combines them in split order (FP64
+// for sums). Output r at out[r].
+struct RowRed {
+  double2* part;           // [S][R] compensated pairs (sums)
+  void* partm;             // [S][R] compute-type maxima
+  unsigned int* tickets;   // one per row range (gridDim.x)
+  void* out;
+  int S;
+};
+
+template <class E, bool ISMAX, int V, int U, int NT>
+__global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int64_t R,
+                                            const int64_t C, const RowRed rr) {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  const int64_t r = (int64_t(blockIdx.x) * NT + threadIdx.x) * V;
+  const int nvalid = clamp_valid(R - r, V);
+  const int s = blockIdx.y;
+  const int64_t cb = C * s / rr.S, ce = C * (s + 1) / rr.S;
+  ThreadSum<CT> acc[V];
+  CT m[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    acc[j].init();
+    m[j] = neg_inf<CT>();
+  }
+  if (nvalid > 0) {
+    for (int64_t c = cb; c < ce; c += U) {
+      Pack<LL, V, CT> p[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c + u < ce) load_rc(p[u], sl, r, c + u, nvalid);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c + u < ce) {
+          CT v[V];
+          eval_lanes<V>(e, p[u], v);
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            if (ISMAX) m[j] = max_nan(m[j], v[j]);
+            else acc[j].add(v[j]);
+          }
+        }
+      }
+    }
+  }
+  CT* out = static_cast<CT*>(rr.out);
+  if (rr.S == 1) {
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      if (j < nvalid) out[r + j] = ISMAX ? m[j] : CT(double(acc[j].s) + double(acc[j].c));
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    if (j < nvalid) {
+      if (ISMAX) static_cast<CT*>(rr.partm)[int64_t(s) * R + r + j] = m[j];
+      else rr.part[int64_t(s) * R + r + j] = make_double2(double(acc[j].s), double(acc[j].c));
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) last = atomicAdd(rr.tickets + blockIdx.x, 1u) == unsigned(rr.S - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    if (j < nvalid) {
+      if (ISMAX) {
+        CT mm = neg_inf<CT>();
+        for (int k = 0; k < rr.S; ++k)
+          mm = max_nan(mm, __ldcg(static_cast<const CT*>(rr.partm) + int64_t(k) * R + r + j));
+        out[r + j] = mm;
+      } else {
+        CompSum<double> a;
+        a.init();
+        for (int k = 0; k < rr.S; ++k) {
+          double2 q = __ldcg(rr.part + int64_t(k) * R + r + j);
+          a.add(q.x);
+          a.add(q.y);
+        }
+        out[r + j] = CT(a.s + a.c);
+      }
+    }
+  }
+  if (threadIdx.x == 0) rr.tickets[blockIdx.x] = 0u;
+}
+
+// ---------------------------------------------------------------- A9: fused backward
+//
+// L = gL * accu(f(leaves)). Per element the tree is re-evaluated and its
+// reverse pass (Leaf/Bin/Un/SL/SR ::bwd) hands each distinct leaf its
+// local partial derivative. Plain leaves get dL/dleaf written element by
+// element; each_col leaves (vectors indexed by row) get their row sums,
+// accumulated per thread and combined across column splits like k_row.
+
+template <class LL, class CT> struct GradAcc {
+  CT g[tl_size<LL>::value];
+  template <int K, int M> FX_D void add(CT a) { g[tl_index<LL, K, M>::value] += a; }
+};
+
+struct GradArgs {
+  void* g[FX_MAX_SLOTS];    // per input slot: dense column-major gradient, or null
+  const void* gscale;       // device scalar (reduction type) or null for 1
+  double2* part;            // [NBC][S][R]
+  unsigned int* tickets;    // one per row range
+  int S;
+};
+
+template <class LL, int I = 0> FX_HD constexpr int count_mode(int mode) {
+  if constexpr (I < tl_size<LL>::value) {
+    return (tl_at<LL, I>::type::mode == mode ? 1 : 0) + count_mode<LL, I + 1>(mode);
+  } else {
+    return 0;
+  }
+}
+template <class LL, int I, int J = 0> FX_HD constexpr int bc_rank() {
+  if constexpr (J < I) {
+    return (tl_at<LL, J>::type::mode == MBC ? 1 : 0) + bc_rank<LL, I, J + 1>();
+  } else {
+    return 0;
+  }
+}
+
+// Writes the plain leaves' gradients at (r.., c) and adds the each_col
+// leaves' partial derivatives to their per-row running sums.
+template <class LL, int V, class CT, int NB, int I = 0>
+FX_D void bwd_store(const GradAcc<LL, CT> (&g)[V], ThreadSum<CT> (&bacc)[NB][V],
+                    const GradArgs& ga, int64_t r, int64_t c, int64_t R, int nvalid) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    if constexpr (L::mode == MN) {
+      T* dst = static_cast<T*>(ga.g[L::slot]);
+      if (dst) {
+        T* q = dst + r + c * R;  // dense, ld = R
+        if (nvalid == V) {
+          Raw<T, V> o;
+#pragma unroll
+          for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(g[j].g[I]);
+          vstore(q, o);
+        } else {
+#pragma unroll
+          for (int j = 0; j < V; ++j)
+            if (j < nvalid) sstore(q + j, narrow_to<T>::from(g[j].g[I]));
+        }
+      }
+    } else if constexpr (L::mode == MBC) {
+      constexpr int b = bc_rank<LL, I>();
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid) bacc[b][j].add(g[j].g[I]);
+    }
+    bwd_store<LL, V, CT, NB, I + 1>(g, bacc, ga, r, c, R, nvalid);
+  }
+}
+
+// Last block of a row range: sum the column splits' row partials in split
+// order (FP64, compensated) and write each_col leaves' gradients (dense).
+template <class LL, int V, class CT, int I = 0>
+FX_D void bwd_bc_finish(const GradArgs& ga, int64_t r, int64_t R, int nvalid) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    if constexpr (L::mode == MBC) {
+      constexpr int b = bc_rank<LL, I>();
+      T* dst = static_cast<T*>(ga.g[L::slot]);
+      if (dst) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          if (j < nvalid) {
+            CompSum<double> a;
+            a.init();
+            for (int k = 0; k < ga.S; ++k) {
+              double2 q = __ldcg(ga.part + (int64_t(b) * ga.S + k) * R + r + j);
+              a.add(q.x);
+              a.add(q.y);
+            }
+            sstore(dst + r + j, narrow_to<T>::from(CT(a.s + a.c)));
+          }
+        }
+      }
+    }
+    bwd_bc_finish<LL, V, CT, I + 1>(ga, r, R, nvalid);
+  }
+}
+
+template <class E, int V, int U, int NT>
+__global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int64_t R,
+                                            const int64_t C, const GradArgs ga) {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  constexpr int NL = tl_size<LL>::value;
+  constexpr int NBC = count_mode<LL>(MBC);
+  static_assert(count_mode<LL>(MT) == 0 && count_mode<LL>(MBR) == 0,
+                "fused backward: plain and each_col leaves only");
+  const int64_t r = (int64_t(blockIdx.x) * NT + threadIdx.x) * V;
+  const int nvalid = clamp_valid(R - r, V);
+  const int s = blockIdx.y;
+  const int64_t cb = C * s / ga.S, ce = C * (s + 1) / ga.S;
+  const CT gL = ga.gscale ? __ldg(static_cast<const CT*>(ga.gscale)) : CT(1);
+  ThreadSum<CT> bacc[NBC > 0 ? NBC : 1][V];
+#pragma unroll
+  for (int b = 0; b < (NBC > 0 ? NBC : 1); ++b)
+#pragma unroll
+    for (int j = 0; j < V; ++j) bacc[b][j].init();
+  if (nvalid > 0) {
+    for (int64_t c = cb; c < ce; c += U) {
+      Pack<LL, V, CT> p[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c + u < ce) load_rc(p[u], sl, r, c + u, nvalid);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c + u < ce) {
+          GradAcc<LL, CT> g[V];
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+#pragma unroll
+            for (int k = 0; k < NL; ++k) g[j].g[k] = CT(0);
+            Ctx<LL, V, CT> cx{p[u], j};
+            e.bwd(cx, gL, g[j]);
+          }
+          bwd_store<LL, V, CT, (NBC > 0 ? NBC : 1)>(g, bacc, ga, r, c + u, R, nvalid);
+        }
+      }
+    }
+  }
+  if constexpr (NBC > 0) {
+#pragma unroll
+    for (int b = 0; b < NBC; ++b)
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid)
+          ga.part[(int64_t(b) * ga.S + s) * R + r + j] =
+              make_double2(double(bacc[b][j].s), double(bacc[b][j].c));
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(ga.tickets + blockIdx.x, 1u) == unsigned(ga.S - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    bwd_bc_finish<LL, V, CT>(ga, r, R, nvalid);
+    if (threadIdx.x == 0) ga.tickets[blockIdx.x] = 0u;
+  }
+}
+
+}  // namespace fx

@@ -1,0 +1,443 @@
+// launch.cuh - host-side drivers: shape checks, choice of kernel family and
+// vector width, grid sizing, workspace layout, the unfused baseline and the
+// autotuner. Everything here is templated on the (normalised) tree type.
+#pragma once
+
+#include <cmath>
+#include <string>
+
+#include "kernels.cuh"
+#include "runtime.hpp"
+
+namespace fx {
+
+// What one evaluation sees: bindings (inputs, then outputs), launch shape,
+// the reduction workspace and a launch counter.
+struct Run {
+  const Binding* b;
+  int n_in;
+  Tune tune;
+  Workspace* ws;
+  int* launches;
+  cudaStream_t st;
+};
+
+inline Run run_of(fx_expr* x, cudaStream_t st) {
+  return Run{x->b, x->e->n_in, x->tune, &x->ws, &x->last_launches, st};
+}
+
+inline bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
+
+inline Slots make_slots(const Binding* b, int n) {
+  Slots s{};
+  for (int k = 0; k < n; ++k) {
+    s.s[k].p = b[k].p;
+    s.s[k].ld = b[k].ld;
+    s.s[k].vs = (b[k].rows == 1 && b[k].cols != 1) ? b[k].ld : 1;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- leaf checks
+
+template <class LL, int I = 0> fx_status check_leaves(const Binding* b, int64_t R, int64_t C) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    const Binding& x = b[L::slot];
+    bool ok = false;
+    const char* want = "";
+    if constexpr (L::mode == MN) {
+      ok = x.rows == R && x.cols == C;
+      want = "R x C";
+    } else if constexpr (L::mode == MT) {
+      ok = x.rows == C && x.cols == R;
+      want = "C x R (transposed)";
+    } else if constexpr (L::mode == MBC) {
+      ok = (x.rows == R && x.cols == 1) || (x.rows == 1 && x.cols == R);
+      want = "a vector of length R (each_col)";
+    } else {
+      ok = (x.rows == C && x.cols == 1) || (x.rows == 1 && x.cols == C);
+      want = "a vector of length C (each_row)";
+    }
+    if (!ok)
+      return fail(FX_E_SHAPE, "slot %d is %lld x %lld; expected %s with R=%lld, C=%lld", L::slot,
+                  (long long)x.rows, (long long)x.cols, want, (long long)R, (long long)C);
+    return check_leaves<LL, I + 1>(b, R, C);
+  }
+  return FX_OK;
+}
+
+// The tree's shape from its first matrix leaf.
+template <class LL, int I = 0> bool infer_shape(const Binding* b, int64_t& R, int64_t& C) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    if constexpr (L::mode == MN) {
+      R = b[L::slot].rows;
+      C = b[L::slot].cols;
+      return true;
+    } else if constexpr (L::mode == MT) {
+      R = b[L::slot].cols;
+      C = b[L::slot].rows;
+      return true;
+    } else {
+      return infer_shape<LL, I + 1>(b, R, C);
+    }
+  }
+  return false;
+}
+
+template <class LL, int I = 0> FX_HD constexpr bool all_mn() {
+  if constexpr (I < tl_size<LL>::value) {
+    return tl_at<LL, I>::type::mode == MN && all_mn<LL, I + 1>();
+  } else {
+    return true;
+  }
+}
+
+// Flat stream needs every leaf dense (ld == rows) and aligned to A bytes.
+template <class LL, int I = 0> bool leaves_flat(const Binding* b, size_t a) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    const Binding& x = b[L::slot];
+    if (!(x.ld == x.rows || x.cols <= 1)) return false;
+    if (!aligned(x.p, a)) return false;
+    return leaves_flat<LL, I + 1>(b, a);
+  }
+  return true;
+}
+template <class LL, int I = 0> bool leaves_dense(const Binding* b) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    const Binding& x = b[L::slot];
+    if (!(x.ld == x.rows || x.cols <= 1)) return false;
+    return leaves_dense<LL, I + 1>(b);
+  }
+  return true;
+}
+
+// Column-vector path: every full V-vector of every matrix leaf is aligned.
+template <class LL, int V, int I = 0> bool leaves_vec(const Binding* b) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    const Binding& x = b[L::slot];
+    const size_t a = sizeof(T) * V;
+    if constexpr (L::mode == MN || L::mode == MT) {
+      if (!aligned(x.p, a) || x.ld % V != 0) return false;
+    } else if constexpr (L::mode == MBC) {
+      const bool unit = !(x.rows == 1 && x.cols != 1);
+      if (unit && !aligned(x.p, a)) return false;
+    }
+    return leaves_vec<LL, V, I + 1>(b);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- launches
+
+template <class K> int grid_for(K kernel, int block, int64_t work, const Tune& t) {
+  const int sms = device_sms() > 0 ? device_sms() : 1;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  const int bps = t.bps > 0 ? (t.bps < occ ? t.bps : occ) : occ;
+  int64_t g = int64_t(sms) * bps;
+  if (g > work) g = work;
+  if (g < 1) g = 1;
+  return int(g);
+}
+
+inline fx_status after_launch(const Run& r, const char* what) {
+  if (inject_launch_failure()) return fail(FX_E_CUDA, "%s: launch failed (injected)", what);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  ++*r.launches;
+  return FX_OK;
+}
+
+// Reduction workspace for `grid` partials plus one ticket.
+inline fx_status red_space(const Run& r, int grid, RedArgs& red) {
+  const size_t part = size_t(grid) * sizeof(double2);
+  FX_TRY(r.ws->ensure(part + 256, r.st));
+  red.part = static_cast<double2*>(r.ws->p);
+  red.ticket = reinterpret_cast<unsigned int*>(static_cast<char*>(r.ws->p) + part);
+  return FX_OK;
+}
+
+template <class E, class Epi, int V, int U>
+fx_status launch_flat_u(const Run& r, const E& e, const Slots& sl, int64_t n, const Epi& epi,
+                        RedArgs red) {
+  auto kern = k_flat<E, Epi, V, U>;
+  const int block = (r.tune.block >= 64 && r.tune.block <= 512) ? r.tune.block : 256;
+  const int64_t nv = n / V;
+  int64_t work = (nv + int64_t(block) * U - 1) / (int64_t(block) * U);
+  const int grid = grid_for(kern, block, work > 0 ? work : 1, r.tune);
+  if constexpr (Epi::reduces) FX_TRY(red_space(r, grid, red));
+  kern<<<grid, block, 0, r.st>>>(e, sl, n, epi, red);
+  return after_launch(r, "k_flat");
+}
+
+template <class E, class Epi, int V>
+fx_status launch_flat(const Run& r, const E& e, const Slots& sl, int64_t n, const Epi& epi,
+                      RedArgs red) {
+  switch (r.tune.unroll) {
+    case 1: return launch_flat_u<E, Epi, V, 1>(r, e, sl, n, epi, red);
+    case 2: return launch_flat_u<E, Epi, V, 2>(r, e, sl, n, epi, red);
+    default: return launch_flat_u<E, Epi, V, 4>(r, e, sl, n, epi, red);
+  }
+}
+
+// Tile shapes: 64 x 64 (32 x 32 for FP64) when a transposed leaf is staged
+// through shared memory; 256 x 16 otherwise (long contiguous column runs).
+template <class E, int V> struct TileCfg {
+  static constexpr bool has_t = count_mt<leaves_t<E>>() > 0;
+  static constexpr bool dbl = std::is_same<ct_of<E>, double>::value;
+  static constexpr int TR = has_t ? (dbl ? 32 : 64) : 256;
+  static constexpr int TC = has_t ? (dbl ? 32 : 64) : 16;
+  static constexpr int NT = 256;
+};
+
+template <class E, class Epi, int V>
+fx_status launch_tile(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C,
+                      const Epi& epi, RedArgs red) {
+  using TC_ = TileCfg<E, V>;
+  auto kern = k_tile<E, Epi, V, TC_::TR, TC_::TC, TC_::NT>;
+  const int64_t ntiles = ((R + TC_::TR - 1) / TC_::TR) * ((C + TC_::TC - 1) / TC_::TC);
+  const int grid = grid_for(kern, TC_::NT, ntiles > 0 ? ntiles : 1, r.tune);
+  if constexpr (Epi::reduces) FX_TRY(red_space(r, grid, red));
+  kern<<<grid, TC_::NT, 0, r.st>>>(e, sl, R, C, epi, red);
+  return after_launch(r, "k_tile");
+}
+
+// ---------------------------------------------------------------- element-wise
+
+template <class T, class E> fx_status run_elementwise(const Run& r, const E& e) {
+  using LL = leaves_t<E>;
+  constexpr int V = vec_width<E, 16>();
+  const Binding& zb = r.b[r.n_in];
+  const int64_t R = zb.rows, C = zb.cols;
+  FX_TRY(check_leaves<LL>(r.b, R, C));
+  if (R * C == 0) return FX_OK;
+  const Slots sl = make_slots(r.b, r.n_in);
+  T* z = static_cast<T*>(zb.p);
+  const bool zdense = zb.ld == R || C == 1;
+  if constexpr (all_mn<LL>()) {
+    if (zdense && leaves_dense<LL>(r.b)) {
+      if (leaves_flat<LL>(r.b, V * sizeof(T)) && aligned(z, V * sizeof(T)))
+        return launch_flat<E, EpiStore<T, V>, V>(r, e, sl, R * C, EpiStore<T, V>{z, R}, {});
+      return launch_flat<E, EpiStore<T, 1>, 1>(r, e, sl, R * C, EpiStore<T, 1>{z, R}, {});
+    }
+  }
+  if (leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0)
+    return launch_tile<E, EpiStore<T, V>, V>(r, e, sl, R, C, EpiStore<T, V>{z, zb.ld}, {});
+  return launch_tile<E, EpiStore<T, 1>, 1>(r, e, sl, R, C, EpiStore<T, 1>{z, zb.ld}, {});
+}
+
+// Element-wise tree plus its accu (outputs Z and s).
+template <class T, class E> fx_status run_multi(const Run& r, const E& e) {
+  using LL = leaves_t<E>;
+  constexpr int V = vec_width<E, 16>();
+  const Binding& zb = r.b[r.n_in];
+  const Binding& sb = r.b[r.n_in + 1];
+  const int64_t R = zb.rows, C = zb.cols;
+  FX_TRY(check_leaves<LL>(r.b, R, C));
+  if (sb.rows * sb.cols != 1) return fail(FX_E_SHAPE, "the accu output must be 1 x 1");
+  const Slots sl = make_slots(r.b, r.n_in);
+  T* z = static_cast<T*>(zb.p);
+  RedArgs red{};
+  red.out = sb.p;
+  const bool zdense = zb.ld == R || C == 1;
+  if constexpr (all_mn<LL>()) {
+    if (zdense && leaves_dense<LL>(r.b)) {
+      if (leaves_flat<LL>(r.b, V * sizeof(T)) && aligned(z, V * sizeof(T)))
+        return launch_flat<E, EpiStoreSum<T, V>, V>(r, e, sl, R * C, EpiStoreSum<T, V>{z, R}, red);
+      return launch_flat<E, EpiStoreSum<T, 1>, 1>(r, e, sl, R * C, EpiStoreSum<T, 1>{z, R}, red);
+    }
+  }
+  if (leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0)
+    return launch_tile<E, EpiStoreSum<T, V>, V>(r, e, sl, R, C, EpiStoreSum<T, V>{z, zb.ld}, red);
+  return launch_tile<E, EpiStoreSum<T, 1>, 1>(r, e, sl, R, C, EpiStoreSum<T, 1>{z, zb.ld}, red);
+}
+
+// ---------------------------------------------------------------- A5: accu, norm
+
+template <class T, class Root> fx_status run_full_reduce(const Run& r, const Root& root) {
+  using E = typename root_of<Root>::inner;
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  constexpr bool SQ = std::is_same<Root, Norm2<E>>::value;
+  constexpr int V = vec_width<E, 16>();
+  const E& e = inner_of(root);
+  int64_t R = 0, C = 0;
+  if (!infer_shape<LL>(r.b, R, C)) return fail(FX_E_SHAPE, "no matrix leaf to take the shape from");
+  FX_TRY(check_leaves<LL>(r.b, R, C));
+  const Binding& ob = r.b[r.n_in];
+  if (ob.rows * ob.cols != 1) return fail(FX_E_SHAPE, "the reduction output must be 1 x 1");
+  const Slots sl = make_slots(r.b, r.n_in);
+  RedArgs red{};
+  red.out = ob.p;
+  if constexpr (all_mn<LL>()) {
+    if (leaves_dense<LL>(r.b)) {
+      if (leaves_flat<LL>(r.b, V * sizeof(T)))
+        return launch_flat<E, EpiSum<CT, V, SQ>, V>(r, e, sl, R * C, EpiSum<CT, V, SQ>{R}, red);
+      return launch_flat<E, EpiSum<CT, 1, SQ>, 1>(r, e, sl, R * C, EpiSum<CT, 1, SQ>{R}, red);
+    }
+  }
+  if (leaves_vec<LL, V>(r.b))
+    return launch_tile<E, EpiSum<CT, V, SQ>, V>(r, e, sl, R, C, EpiSum<CT, V, SQ>{0}, red);
+  return launch_tile<E, EpiSum<CT, 1, SQ>, 1>(r, e, sl, R, C, EpiSum<CT, 1, SQ>{0}, red);
+}
+
+// ---------------------------------------------------------------- A6: sum / max along a dim
+
+template <class Root> struct dim_of;
+template <class E, int D> struct dim_of<SumDim<E, D>> { static constexpr int d = D; static constexpr bool ismax = false; };
+template <class E, int D> struct dim_of<MaxDim<E, D>> { static constexpr int d = D; static constexpr bool ismax = true; };
+
+template <class E, bool ISMAX, int V>
+fx_status launch_col(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C, void* out,
+                     int64_t ldo) {
+  constexpr int NT = 256, U = 4;
+  if (R >= 1024) {
+    auto kern = k_col<E, ISMAX, V, U, NT, NT>;
+    const int grid = grid_for(kern, NT, C > 0 ? C : 1, r.tune);
+    kern<<<grid, NT, 0, r.st>>>(e, sl, R, C, out, ldo);
+  } else {
+    auto kern = k_col<E, ISMAX, V, U, 32, NT>;
+    const int64_t work = (C + NT / 32 - 1) / (NT / 32);
+    const int grid = grid_for(kern, NT, work > 0 ? work : 1, r.tune);
+    kern<<<grid, NT, 0, r.st>>>(e, sl, R, C, out, ldo);
+  }
+  return after_launch(r, "k_col");
+}
+
+template <class E, bool ISMAX, int V>
+fx_status launch_row(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C, void* out) {
+  using CT = ct_of<E>;
+  constexpr int NT = 256, U = 4;
+  auto kern = k_row<E, ISMAX, V, U, NT>;
+  const int64_t gx = (R + int64_t(NT) * V - 1) / (int64_t(NT) * V);
+  const int sms = device_sms() > 0 ? device_sms() : 1;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1) occ = 1;
+  const int bps = r.tune.bps > 0 ? (r.tune.bps < occ ? r.tune.bps : occ) : occ;
+  const int64_t target = int64_t(sms) * bps;
+  int64_t S = (target + gx - 1) / gx;
+  const int64_t smax = C / (2 * U) > 1 ? C / (2 * U) : 1;
+  if (S > smax) S = smax;
+  if (S > 65535) S = 65535;
+  if (S < 1) S = 1;
+  RowRed rr{};
+  rr.out = out;
+  rr.S = int(S);
+  if (S > 1) {
+    const size_t part = size_t(S) * R * sizeof(double2);
+    const size_t partm = size_t(S) * R * sizeof(CT);
+    const size_t tick = size_t(gx) * sizeof(unsigned int);
+    FX_TRY(r.ws->ensure(part + partm + tick + 512, r.st));
+    char* w = static_cast<char*>(r.ws->p);
+    rr.part = reinterpret_cast<double2*>(w);
+    rr.partm = w + part;
+    rr.tickets = reinterpret_cast<unsigned int*>(w + ((part + partm + 255) & ~size_t(255)));
+  }
+  kern<<<dim3(unsigned(gx > 0 ? gx : 1), unsigned(S)), NT, 0, r.st>>>(e, sl, R, C, rr);
+  return after_launch(r, "k_row");
+}
+
+template <class T, class Root> fx_status run_dim_reduce(const Run& r, const Root& root) {
+  using E = typename root_of<Root>::inner;
+  using LL = leaves_t<E>;
+  constexpr int D = dim_of<Root>::d;
+  constexpr bool ISMAX = dim_of<Root>::ismax;
+  constexpr int V = vec_width<E, 16>();
+  static_assert(count_mt<LL>() == 0, "dim reductions over transposed leaves are not fused");
+  const E& e = inner_of(root);
+  int64_t R = 0, C = 0;
+  if (!infer_shape<LL>(r.b, R, C)) return fail(FX_E_SHAPE, "no matrix leaf to take the shape from");
+  FX_TRY(check_leaves<LL>(r.b, R, C));
+  const Binding& ob = r.b[r.n_in];
+  const Slots sl = make_slots(r.b, r.n_in);
+  if (D == 0) {
+    if (!(ob.rows == 1 && ob.cols == C)) return fail(FX_E_SHAPE, "sum/max along dim 0 gives 1 x %lld", (long long)C);
+    if (C == 0) return FX_OK;
+    if (leaves_vec<LL, V>(r.b)) return launch_col<E, ISMAX, V>(r, e, sl, R, C, ob.p, ob.ld);
+    return launch_col<E, ISMAX, 1>(r, e, sl, R, C, ob.p, ob.ld);
+  }
+  if (!(ob.rows == R && ob.cols == 1)) return fail(FX_E_SHAPE, "sum/max along dim 1 gives %lld x 1", (long long)R);
+  if (R == 0) return FX_OK;
+  if (leaves_vec<LL, V>(r.b)) return launch_row<E, ISMAX, V>(r, e, sl, R, C, ob.p);
+  return launch_row<E, ISMAX, 1>(r, e, sl, R, C, ob.p);
+}
+
+// ---------------------------------------------------------------- root dispatch
+
+template <class T, class Root> fx_status run_root(const Run& r, const Root& root, int kind) {
+  static_assert(!has_prod_v<Root>, "a matrix product is a fusion boundary");
+  if (kind == FX_KIND_MULTI) {
+    if constexpr (root_of<Root>::kind == FX_KIND_ELEMENTWISE) return run_multi<T>(r, root);
+    return fail(FX_E_UNSUPPORTED, "multi-output needs an element-wise tree");
+  }
+  if constexpr (root_of<Root>::kind == FX_KIND_ELEMENTWISE) return run_elementwise<T>(r, root);
+  else if constexpr (root_of<Root>::kind == FX_KIND_FULL_REDUCE) return run_full_reduce<T>(r, root);
+  else return run_dim_reduce<T>(r, root);
+}
+
+// ---------------------------------------------------------------- A9: backward
+
+template <class T, class Root>
+fx_status run_backward(fx_expr* x, const Root& root, const void* gout, void* const* grads,
+                       cudaStream_t st) {
+  if constexpr (!std::is_same<Root, Accu<typename root_of<Root>::inner>>::value) {
+    return fail(FX_E_UNSUPPORTED, "fused backward needs an accu(...) root");
+  } else {
+    using E = typename root_of<Root>::inner;
+    using LL = leaves_t<E>;
+    constexpr int V = vec_width<E, 16>();
+    constexpr int NT = 256, U = 2;
+    constexpr int NBC = count_mode<LL>(MBC);
+    const Run r = run_of(x, st);
+    const E& e = inner_of(root);
+    int64_t R = 0, C = 0;
+    if (!infer_shape<LL>(r.b, R, C)) return fail(FX_E_SHAPE, "no matrix leaf to take the shape from");
+    FX_TRY(check_leaves<LL>(r.b, R, C));
+    GradArgs ga{};
+    bool vec = leaves_vec<LL, V>(r.b) && R % V == 0;
+    for (int k = 0; k < r.n_in; ++k) {
+      ga.g[k] = grads[k];
+      if (grads[k] && !aligned(grads[k], sizeof(T))) return fail(FX_E_ALIGN, "gradient %d misaligned", k);
+      if (grads[k] && !aligned(grads[k], sizeof(T) * V)) vec = false;
+    }
+    ga.gscale = gout;
+    if (R * C == 0) {
+      // gradients of an empty sum are zero
+      for (int k = 0; k < r.n_in; ++k)
+        if (grads[k]) FX_CUDA(cudaMemsetAsync(grads[k], 0, size_t(r.b[k].rows) * r.b[k].cols * sizeof(T), st));
+      return FX_OK;
+    }
+    const Slots sl = make_slots(r.b, r.n_in);
+    auto go = [&](auto kern, int v) -> fx_status {
+      const int64_t gx = (R + int64_t(NT) * v - 1) / (int64_t(NT) * v);
+      const int sms = device_sms() > 0 ? device_sms() : 1;
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1) occ = 1;
+      int64_t S = (int64_t(sms) * occ + gx - 1) / gx;
+      const int64_t smax = C / (2 * U) > 1 ? C / (2 * U) : 1;
+      if (S > smax) S = smax;
+      if (S > 65535) S = 65535;
+      if (S < 1) S = 1;
+      ga.S = int(S);
+      if (NBC > 0) {
+        const size_t part = size_t(NBC) * S * R * sizeof(double2);
+        FX_TRY(x->ws.ensure(part + size_t(gx) * 4 + 512, st));
+        ga.part = static_cast<double2*>(x->ws.p);
+        ga.tickets = reinterpret_cast<unsigned int*>(static_cast<char*>(x->ws.p) + ((part + 255) & ~size_t(255)));
+      }
+      kern<<<dim3(unsigned(gx), unsigned(S)), NT, 0, st>>>(e, sl, R, C, ga);
+      return after_launch(r, "k_bwd");
+    };
+    if (vec) return go(k_bwd<E, V, U, NT>, V);
+    return go(k_bwd<E, 1, U, NT>, 1);
+  }
+}
+
+}  // namespace fx

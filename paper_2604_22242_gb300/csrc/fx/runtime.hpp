@@ -1,0 +1,121 @@
+// runtime.hpp - host-side state behind the C ABI: the expression object,
+// its device workspace, the registry of compiled instantiations, tuning
+// state and error reporting.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fx.h"
+
+namespace fx {
+
+struct Binding {
+  void* p = nullptr;
+  int64_t rows = 0, cols = 0, ld = 0;
+  bool bound = false;
+};
+
+// Launch shape: threads per block, vectors per thread per step (flat and
+// dim kernels), blocks per SM (0: as many as fit).
+struct Tune {
+  int block = 256;
+  int unroll = 4;
+  int bps = 0;
+  bool tuned = false;
+};
+
+// Device workspace owned by one fx_expr: reduction partials, tickets,
+// unfused intermediates, batch descriptors. Grown on demand with
+// stream-ordered allocation; new bytes are zeroed (tickets start at 0).
+struct Workspace {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  fx_status ensure(size_t need, cudaStream_t st);
+  void release();
+};
+
+struct BatchCache;  // batch.cuh
+
+struct Entry;
+
+}  // namespace fx
+
+struct fx_expr {
+  const fx::Entry* e = nullptr;
+  fx::Binding b[FX_MAX_SLOTS];
+  double scal[FX_MAX_SCALARS] = {};
+  fx::Workspace ws;
+  fx::Workspace ws_tmp;  // unfused intermediates
+  fx::Tune tune;
+  int last_launches = 0;
+  fx::BatchCache* batch = nullptr;
+};
+
+namespace fx {
+
+using EvalFn = fx_status (*)(fx_expr*, cudaStream_t);
+using HostFn = fx_status (*)(fx_expr*, const void* const*, void* const*, cudaStream_t);
+using BatchFn = fx_status (*)(fx_expr*, int64_t, const fx_batch_item*, cudaStream_t, int);
+using BwdFn = fx_status (*)(fx_expr*, const void*, void* const*, cudaStream_t);
+using TuneFn = fx_status (*)(fx_expr*, int, cudaStream_t);
+using FreeFn = void (*)(fx_expr*);
+
+struct Entry {
+  const char* name;
+  const char* formula;
+  fx_dtype storage;
+  int n_in, n_out, n_scal;
+  fx_kind kind;
+  const char* const* slot_names;
+  const double* defaults;
+  EvalFn eval;
+  EvalFn eval_unfused;
+  BatchFn eval_batch;     // may be null
+  BwdFn eval_backward;    // may be null
+  TuneFn tune;
+};
+
+std::vector<Entry>& registry();
+struct Registrar {
+  explicit Registrar(const Entry& e) { registry().push_back(e); }
+};
+
+// errors: thread-local message, returned status
+fx_status fail(fx_status s, const char* fmt, ...);
+fx_status cuda_fail(cudaError_t err, const char* what);
+#define FX_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t fx_err_ = (call);                              \
+    if (fx_err_ != cudaSuccess) return ::fx::cuda_fail(fx_err_, #call); \
+  } while (0)
+#define FX_TRY(call)                     \
+  do {                                   \
+    fx_status fx_st_ = (call);           \
+    if (fx_st_ != FX_OK) return fx_st_;  \
+  } while (0)
+
+// Number of SMs of the current device (cached per device).
+int device_sms();
+// Name of the current device (for the tuning cache key).
+std::string device_name();
+
+size_t storage_bytes(fx_dtype d);
+size_t reduce_bytes(fx_dtype d);
+
+// Tuning cache: key -> "block,unroll,bps"
+bool tune_cache_get(const std::string& key, Tune& t);
+void tune_cache_put(const std::string& key, const Tune& t);
+
+// Frees an expression's batch descriptors and CUDA graph (batch.cu).
+void free_batch_cache(fx_expr* x);
+
+// Test hook for host-side fault injection: FX_INJECT=launch_fail makes
+// every launch helper report a failed launch without launching.
+bool inject_launch_failure();
+
+}  // namespace fx

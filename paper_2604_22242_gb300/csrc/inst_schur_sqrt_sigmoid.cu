@@ -1,0 +1,8 @@
+// Build-time instantiation of one expression tree for its storage types.
+#include "fx/defs.cuh"
+
+namespace fx {
+namespace defs {
+FX_REGISTER(SchurSqrtSigmoid)
+}  // namespace defs
+}  // namespace fx

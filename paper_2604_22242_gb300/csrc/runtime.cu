@@ -1,0 +1,382 @@
+// runtime.cu - the C ABI (include/fx.h) over the registry of compiled trees.
+//
+// Host code only: argument checks, bindings, workspace, errors, the tuning
+// cache file. The kernels live in the instantiation units (inst_*.cu).
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+#include "fx/runtime.hpp"
+
+namespace fx {
+
+static thread_local std::string g_err;
+
+fx_status fail(fx_status s, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+fx_status cuda_fail(cudaError_t err, const char* what) {
+  return fail(FX_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+std::vector<Entry>& registry() {
+  static std::vector<Entry> r;
+  return r;
+}
+
+int device_sms() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cache[dev] = n;
+  return n;
+}
+
+std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp p;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess)
+    return "unknown";
+  return p.name;
+}
+
+size_t storage_bytes(fx_dtype d) {
+  switch (d) {
+    case FX_F32: return 4;
+    case FX_F64: return 8;
+    case FX_BF16:
+    case FX_F16: return 2;
+  }
+  return 0;
+}
+size_t reduce_bytes(fx_dtype d) { return d == FX_F64 ? 8 : 4; }
+
+bool inject_launch_failure() {
+  const char* v = getenv("FX_INJECT");
+  return v && strcmp(v, "launch_fail") == 0;
+}
+
+fx_status Workspace::ensure(size_t need, cudaStream_t st) {
+  if (need <= bytes && p) return FX_OK;
+  if (const char* v = getenv("FX_INJECT"); v && strcmp(v, "alloc_fail") == 0)
+    return fail(FX_E_NOMEM, "workspace allocation failed (injected)");
+  size_t want = need < 4096 ? 4096 : need;
+  want = (want + 255) & ~size_t(255);
+  if (p) {
+    cudaError_t e = cudaFreeAsync(p, stream ? stream : st);
+    p = nullptr;
+    bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(workspace)");
+  }
+  cudaError_t e = cudaMallocAsync(&p, want, st);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return fail(FX_E_NOMEM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(p, 0, want, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
+  bytes = want;
+  stream = st;
+  return FX_OK;
+}
+
+void Workspace::release() {
+  if (p) {
+    // The caller guarantees no launch of this object is in flight.
+    cudaFree(p);
+  }
+  p = nullptr;
+  bytes = 0;
+}
+
+// ---------------------------------------------------------------- tuning cache
+
+static std::string cache_path() {
+  const char* v = getenv("FX_TUNE_CACHE");
+  return v && *v ? v : "fx_tune.json";
+}
+
+// The file is a flat JSON object {"key": "block,unroll,bps", ...}.
+static std::map<std::string, std::string> read_cache() {
+  std::map<std::string, std::string> m;
+  std::ifstream f(cache_path());
+  if (!f) return m;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string s = ss.str();
+  size_t i = 0;
+  auto next_str = [&](std::string& out) -> bool {
+    size_t a = s.find('"', i);
+    if (a == std::string::npos) return false;
+    size_t b = s.find('"', a + 1);
+    if (b == std::string::npos) return false;
+    out = s.substr(a + 1, b - a - 1);
+    i = b + 1;
+    return true;
+  };
+  std::string k, v;
+  while (next_str(k) && next_str(v)) m[k] = v;
+  return m;
+}
+
+static std::mutex g_cache_mu;
+
+bool tune_cache_get(const std::string& key, Tune& t) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  auto m = read_cache();
+  auto it = m.find(key);
+  if (it == m.end()) return false;
+  int b = 0, u = 0, s = 0;
+  if (sscanf(it->second.c_str(), "%d,%d,%d", &b, &u, &s) != 3) return false;
+  t.block = b;
+  t.unroll = u;
+  t.bps = s;
+  t.tuned = true;
+  return true;
+}
+
+void tune_cache_put(const std::string& key, const Tune& t) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  auto m = read_cache();
+  char v[64];
+  snprintf(v, sizeof v, "%d,%d,%d", t.block, t.unroll, t.bps);
+  m[key] = v;
+  std::ofstream f(cache_path());
+  f << "{\n";
+  size_t n = 0;
+  for (auto& kv : m) f << "  \"" << kv.first << "\": \"" << kv.second << "\"" << (++n < m.size() ? ",\n" : "\n");
+  f << "}\n";
+}
+
+}  // namespace fx
+
+using namespace fx;
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int fx_list_count(void) { return int(registry().size()); }
+
+fx_status fx_list_get(int i, const char** name, fx_dtype* storage, const char** formula) {
+  if (i < 0 || i >= int(registry().size())) return fail(FX_E_ARG, "index %d out of range", i);
+  const Entry& e = registry()[i];
+  if (name) *name = e.name;
+  if (storage) *storage = e.storage;
+  if (formula) *formula = e.formula;
+  return FX_OK;
+}
+
+fx_status fx_expr_create(const char* name, fx_dtype storage, fx_expr** out) {
+  if (!name || !out) return fail(FX_E_ARG, "null argument");
+  *out = nullptr;
+  if (storage < FX_F32 || storage > FX_F16) return fail(FX_E_ARG, "bad storage type %d", int(storage));
+  bool known = false;
+  for (const Entry& e : registry()) {
+    if (strcmp(e.name, name) != 0) continue;
+    known = true;
+    if (e.storage != storage) continue;
+    fx_expr* x = new (std::nothrow) fx_expr;
+    if (!x) return fail(FX_E_NOMEM, "out of host memory");
+    x->e = &e;
+    for (int k = 0; k < e.n_scal; ++k) x->scal[k] = e.defaults[k];
+    *out = x;
+    return FX_OK;
+  }
+  if (known) return fail(FX_E_DTYPE, "'%s' is not compiled for storage type %d", name, int(storage));
+  return fail(FX_E_NOTFOUND, "no expression named '%s'", name);
+}
+
+fx_status fx_expr_destroy(fx_expr* x) {
+  if (!x) return FX_OK;
+  free_batch_cache(x);
+  x->ws.release();
+  x->ws_tmp.release();
+  delete x;
+  return FX_OK;
+}
+
+fx_status fx_expr_info(const fx_expr* x, int* n_inputs, int* n_outputs, int* n_scalars,
+                       fx_kind* kind) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  if (n_inputs) *n_inputs = x->e->n_in;
+  if (n_outputs) *n_outputs = x->e->n_out;
+  if (n_scalars) *n_scalars = x->e->n_scal;
+  if (kind) *kind = x->e->kind;
+  return FX_OK;
+}
+
+fx_status fx_expr_slot_name(const fx_expr* x, int slot, const char** name) {
+  if (!x || !name) return fail(FX_E_ARG, "null argument");
+  if (slot < 0 || slot >= x->e->n_in + x->e->n_out) return fail(FX_E_ARG, "slot %d out of range", slot);
+  *name = x->e->slot_names[slot];
+  return FX_OK;
+}
+
+fx_status fx_expr_bind(fx_expr* x, int slot, void* dev_ptr, int64_t rows, int64_t cols, int64_t ld) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  const Entry& e = *x->e;
+  if (slot < 0 || slot >= e.n_in + e.n_out) return fail(FX_E_ARG, "slot %d out of range", slot);
+  if (rows < 0 || cols < 0) return fail(FX_E_SHAPE, "negative shape %lld x %lld", (long long)rows, (long long)cols);
+  if (ld < (rows > 1 ? rows : 1)) return fail(FX_E_ARG, "ld %lld < rows %lld", (long long)ld, (long long)rows);
+  if (rows * cols > 0 && !dev_ptr) return fail(FX_E_ARG, "null pointer for a non-empty buffer");
+  const bool reduce_out = slot >= e.n_in && e.kind != FX_KIND_ELEMENTWISE &&
+                          !(e.kind == FX_KIND_MULTI && slot == e.n_in);
+  const size_t es = reduce_out ? reduce_bytes(e.storage) : storage_bytes(e.storage);
+  if (reinterpret_cast<uintptr_t>(dev_ptr) % es != 0)
+    return fail(FX_E_ALIGN, "slot %d: pointer not aligned to its %zu-byte element", slot, es);
+  Binding& b = x->b[slot];
+  b.p = dev_ptr;
+  b.rows = rows;
+  b.cols = cols;
+  b.ld = ld;
+  b.bound = true;
+  return FX_OK;
+}
+
+fx_status fx_expr_set_scalar(fx_expr* x, int idx, double v) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  if (idx < 0 || idx >= x->e->n_scal) return fail(FX_E_ARG, "scalar %d out of range", idx);
+  x->scal[idx] = v;
+  return FX_OK;
+}
+
+fx_status fx_expr_get_scalar(const fx_expr* x, int idx, double* v) {
+  if (!x || !v) return fail(FX_E_ARG, "null argument");
+  if (idx < 0 || idx >= x->e->n_scal) return fail(FX_E_ARG, "scalar %d out of range", idx);
+  *v = x->scal[idx];
+  return FX_OK;
+}
+
+static fx_status check_bound(const fx_expr* x, int first, int count) {
+  for (int k = first; k < first + count; ++k)
+    if (!x->b[k].bound) return fail(FX_E_UNBOUND, "slot %d (%s) is not bound", k, x->e->slot_names[k]);
+  return FX_OK;
+}
+
+fx_status fx_eval(fx_expr* x, void* stream) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  FX_TRY(check_bound(x, 0, x->e->n_in + x->e->n_out));
+  x->last_launches = 0;
+  return x->e->eval(x, static_cast<cudaStream_t>(stream));
+}
+
+fx_status fx_eval_unfused(fx_expr* x, void* stream) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  FX_TRY(check_bound(x, 0, x->e->n_in + x->e->n_out));
+  x->last_launches = 0;
+  return x->e->eval_unfused(x, static_cast<cudaStream_t>(stream));
+}
+
+fx_status fx_eval_host(fx_expr* x, const void* const* host_in, void* const* host_out, void* stream) {
+  if (!x || !host_in || !host_out) return fail(FX_E_ARG, "null argument");
+  const Entry& e = *x->e;
+  FX_TRY(check_bound(x, 0, e.n_in + e.n_out));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < e.n_in + e.n_out; ++k) {
+    const Binding& b = x->b[k];
+    const bool reduce_out = k >= e.n_in && e.kind != FX_KIND_ELEMENTWISE &&
+                            !(e.kind == FX_KIND_MULTI && k == e.n_in);
+    const size_t es = reduce_out ? reduce_bytes(e.storage) : storage_bytes(e.storage);
+    const size_t width = size_t(b.rows) * es, pitch = size_t(b.ld) * es;
+    if (b.rows * b.cols == 0) continue;
+    if (k < e.n_in) {
+      if (!host_in[k]) return fail(FX_E_ARG, "null host input %d", k);
+      if (pitch == width)
+        FX_CUDA(cudaMemcpyAsync(b.p, host_in[k], width * b.cols, cudaMemcpyHostToDevice, st));
+      else
+        FX_CUDA(cudaMemcpy2DAsync(b.p, pitch, host_in[k], width, width, b.cols, cudaMemcpyHostToDevice, st));
+    }
+  }
+  x->last_launches = 0;
+  FX_TRY(e.eval(x, st));
+  for (int k = e.n_in; k < e.n_in + e.n_out; ++k) {
+    const Binding& b = x->b[k];
+    const bool reduce_out = e.kind != FX_KIND_ELEMENTWISE && !(e.kind == FX_KIND_MULTI && k == e.n_in);
+    const size_t es = reduce_out ? reduce_bytes(e.storage) : storage_bytes(e.storage);
+    const size_t width = size_t(b.rows) * es, pitch = size_t(b.ld) * es;
+    if (b.rows * b.cols == 0) continue;
+    void* h = host_out[k - e.n_in];
+    if (!h) return fail(FX_E_ARG, "null host output %d", k - e.n_in);
+    if (pitch == width)
+      FX_CUDA(cudaMemcpyAsync(h, b.p, width * b.cols, cudaMemcpyDeviceToHost, st));
+    else
+      FX_CUDA(cudaMemcpy2DAsync(h, width, b.p, pitch, width, b.cols, cudaMemcpyDeviceToHost, st));
+  }
+  return FX_OK;
+}
+
+fx_status fx_eval_batch(fx_expr* x, int64_t n, const fx_batch_item* items, void* stream, int use_graph) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  if (n < 0 || (n > 0 && !items)) return fail(FX_E_ARG, "bad batch");
+  if (!x->e->eval_batch) return fail(FX_E_UNSUPPORTED, "'%s' has no batched entry", x->e->name);
+  x->last_launches = 0;
+  return x->e->eval_batch(x, n, items, static_cast<cudaStream_t>(stream), use_graph);
+}
+
+fx_status fx_eval_backward(fx_expr* x, const void* grad_out, void* const* grad_ptrs, void* stream) {
+  if (!x || !grad_ptrs) return fail(FX_E_ARG, "null argument");
+  if (!x->e->eval_backward) return fail(FX_E_UNSUPPORTED, "'%s' has no fused backward", x->e->name);
+  FX_TRY(check_bound(x, 0, x->e->n_in));
+  x->last_launches = 0;
+  return x->e->eval_backward(x, grad_out, grad_ptrs, static_cast<cudaStream_t>(stream));
+}
+
+fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  if (mode < FX_TUNE_OFF || mode > FX_TUNE_SEARCH) return fail(FX_E_ARG, "bad tune mode");
+  if (mode == FX_TUNE_OFF) {
+    x->tune = Tune{};
+    return FX_OK;
+  }
+  FX_TRY(check_bound(x, 0, x->e->n_in + x->e->n_out));
+  return x->e->tune(x, int(mode), static_cast<cudaStream_t>(stream));
+}
+
+fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* bps) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  if (block) *block = x->tune.block;
+  if (unroll) *unroll = x->tune.unroll;
+  if (bps) *bps = x->tune.bps;
+  return FX_OK;
+}
+
+int fx_expr_last_launches(const fx_expr* x) { return x ? x->last_launches : 0; }
+
+const char* fx_last_error_string(void) { return g_err.c_str(); }
+
+const char* fx_status_string(fx_status s) {
+  switch (s) {
+    case FX_OK: return "ok";
+    case FX_E_ARG: return "bad argument";
+    case FX_E_SHAPE: return "shape mismatch";
+    case FX_E_DTYPE: return "storage type not compiled";
+    case FX_E_ALIGN: return "misaligned pointer";
+    case FX_E_UNBOUND: return "unbound slot";
+    case FX_E_UNSUPPORTED: return "unsupported for this expression";
+    case FX_E_CUDA: return "CUDA error";
+    case FX_E_NOMEM: return "out of memory";
+    case FX_E_NOTFOUND: return "no such expression";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -119,7 +119,7 @@ class Buffer:
 def matrix(rng: np.random.Generator, rows: int, cols: int, dist: str, storage: str,
            ld: int | None = None, fill: float = 0.0) -> Buffer:
     """One matrix; padding rows (``ld > rows``) hold ``fill`` and are never drawn."""
-    ld = rows if ld is None else ld
+    ld = max(rows, 1) if ld is None else ld
     if ld < max(rows, 1):
         raise ValueError("ld must be >= rows")
     vals = draw(rng, rows * cols, dist)

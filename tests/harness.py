@@ -1,0 +1,243 @@
+"""Test harness: runs a compiled tree through the C ABI on synth inputs and
+compares it with the FP64 oracle using the scaled error metric.
+
+err_i = |gpu_i - oracle_i| / max(sigma_i, |oracle_i|, tiny)
+
+where sigma is the oracle's running error bound (oracle.at_sigma). Outputs
+whose oracle value overflows the storage type must come out as an infinity
+of the same sign and are left out of the maximum; for FP16 outputs below
+the smallest normal the check is absolute (2^-24).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import synth
+
+STORAGE_CODE = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
+MAXFIN = {"f32": float(np.finfo(np.float32).max), "f64": float(np.finfo(np.float64).max),
+          "bf16": float.fromhex("0x1.fep127"), "f16": 65504.0}
+TINY = {"f32": 2.0**-126, "f64": 2.0**-1022, "bf16": 2.0**-126, "f16": 2.0**-14}
+
+# Oracle trees for the compiled expressions (written from the paper's
+# notation, independently of the library's own formula strings).
+TREES = {
+    "schur_exp_trans": "(- (+ (% A B) (* {s0} (exp C))) (t D))",
+    "sqdiff_accu": "(accu (square (- A B)))",
+    "schur_sqrt_sigmoid": "(+ (% X Y) (/ (sqrt (abs W)) (+ {s0} (exp (neg V)))))",
+    "schur_colsum": "(sum (% X Y) 0)",
+    "absdiff_rowmax": "(max (abs (- X Y)) 1)",
+    "diff_norm": "(norm (- X Y))",
+    "schur_trans_accu": "(+ (% A B) (* {s0} (t C)))",
+    "sigmoid_sqloss": "(accu (square (- (sigmoid (+ (% X W) (each_col b))) Y)))",
+}
+DEFAULT_SCALARS = {"schur_exp_trans": [3.5], "schur_sqrt_sigmoid": [1.0],
+                   "schur_trans_accu": [0.5]}
+SLOTS = {
+    "schur_exp_trans": ["A", "B", "C", "D"],
+    "sqdiff_accu": ["A", "B"],
+    "schur_sqrt_sigmoid": ["X", "Y", "W", "V"],
+    "schur_colsum": ["X", "Y"],
+    "absdiff_rowmax": ["X", "Y"],
+    "diff_norm": ["X", "Y"],
+    "schur_trans_accu": ["A", "B", "C"],
+    "sigmoid_sqloss": ["X", "W", "Y", "b"],
+}
+TRANSPOSED = {"schur_exp_trans": {"D"}, "schur_trans_accu": {"C"}}
+VECTORS = {"sigmoid_sqloss": {"b"}}
+
+TOL_EW = {"f64": 1e-13, "f32": 2e-6, "bf16": 8e-3, "f16": 1e-3}
+TOL_TRANS = {"f64": 1e-13, "f32": 1e-5, "bf16": 8e-3, "f16": 1e-3}
+# reductions of every storage type come out in FP32 (FP64 for f64) from a
+# compensated FP32 accumulation, so they are held to the FP32 reduction bound
+TOL_RED = {"f64": 1e-13, "f32": 1e-5, "bf16": 1e-5, "f16": 1e-5}
+HAS_TRANSCENDENTAL = {"schur_exp_trans", "schur_sqrt_sigmoid", "sigmoid_sqloss"}
+
+
+def tree_of(name, scalars=None):
+    s = scalars if scalars is not None else DEFAULT_SCALARS.get(name, [])
+    return TREES[name].format(**{f"s{i}": repr(float(v)) for i, v in enumerate(s)})
+
+
+def specs_for(name, R, C):
+    out = []
+    for s in SLOTS[name]:
+        if s in TRANSPOSED.get(name, ()):
+            out.append((s, C, R))
+        elif s in VECTORS.get(name, ()):
+            out.append((s, R, 1))
+        else:
+            out.append((s, R, C))
+    return out
+
+
+def tolerance(name, storage, output="Z"):
+    if output != "Z" or name in ("sqdiff_accu", "schur_colsum", "diff_norm", "sigmoid_sqloss"):
+        return TOL_RED[storage]
+    if name in HAS_TRANSCENDENTAL:
+        return TOL_TRANS[storage]
+    return TOL_EW[storage]
+
+
+# ---------------------------------------------------------------- device side
+
+def to_device(buf: synth.Buffer, pad: int = 0):
+    """Flat device copy of a synth buffer (plus `pad` trailing elements)."""
+    import torch
+    data = buf.data
+    if buf.storage == "bf16":
+        t = torch.from_numpy(data.view(np.int16).copy()).view(torch.bfloat16)
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(data))
+    if pad:
+        t = torch.cat([t, torch.zeros(pad, dtype=t.dtype)])
+    return t.cuda()
+
+
+def from_device(t, storage) -> np.ndarray:
+    import torch
+    if t.dtype == torch.bfloat16:
+        return synth.to_f64(t.view(torch.int16).cpu().numpy().view(np.uint16), "bf16")
+    return t.double().cpu().numpy()
+
+
+def torch_dtype(storage):
+    import torch
+    return {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16,
+            "f16": torch.float16}[storage]
+
+
+def canary_buffer(n, dtype, guard=64):
+    import torch
+    t = torch.empty(n + guard, dtype=dtype, device="cuda")
+    t.fill_(float("nan"))
+    return t
+
+
+def check_canary(t, start, guard=64):
+    import torch
+    tail = t[start:start + guard]
+    assert bool(torch.isnan(tail.float()).all()), "write past the end of an output"
+
+
+def run(fx, name, storage, env, R, C, ldz=None, offset=0, unfused=False, scalars=None,
+        stream=None):
+    """Evaluates `name` on device copies of `env`; returns the outputs as FP64."""
+    import torch
+    h = fx.fx_expr_create(name, STORAGE_CODE[storage])
+    try:
+        n_in, n_out, n_scal, kind = fx.fx_expr_info(h)
+        if scalars is not None:
+            for i, v in enumerate(scalars):
+                fx.fx_expr_set_scalar(h, i, v)
+        keep = []
+        for k, s in enumerate(SLOTS[name]):
+            b = env[s]
+            t = to_device(b, pad=offset)
+            if offset:
+                t = t.roll(offset)  # data starts `offset` elements in (misaligned base)
+            keep.append(t)
+            fx.fx_expr_bind(h, k, t.data_ptr() + offset * t.element_size(), b.rows, b.cols, b.ld)
+        outs = {}
+        rdt = torch.float64 if storage == "f64" else torch.float32
+        if kind in ("elementwise", "multi"):
+            ldz = R if ldz is None else ldz
+            z = canary_buffer(max(ldz, 1) * C, torch_dtype(storage))
+            fx.fx_expr_bind(h, n_in, z.data_ptr(), R, C, max(ldz, 1))
+            outs["Z"] = (z, "z")
+        if kind in ("full_reduce", "multi"):
+            s = canary_buffer(1, rdt)
+            fx.fx_expr_bind(h, n_in + (1 if kind == "multi" else 0), s.data_ptr(), 1, 1, 1)
+            outs["s"] = (s, "s")
+        if kind == "dim_reduce":
+            d = 0 if name == "schur_colsum" else 1
+            if d == 0:
+                v = canary_buffer(C, rdt)
+                fx.fx_expr_bind(h, n_in, v.data_ptr(), 1, C, 1)
+            else:
+                v = canary_buffer(R, rdt)
+                fx.fx_expr_bind(h, n_in, v.data_ptr(), R, 1, max(R, 1))
+            outs["v"] = (v, "v")
+        sp = 0 if stream is None else stream
+        if unfused:
+            fx.fx_eval_unfused(h, sp)
+        else:
+            fx.fx_eval(h, sp)
+        torch.cuda.synchronize()
+        launches = fx.fx_expr_last_launches(h)
+        result = {}
+        for key, (t, kindk) in outs.items():
+            if kindk == "z":
+                ldzz = max(ldz, 1)
+                check_canary(t, ldzz * C)
+                full = from_device(t[: ldzz * C], storage)
+                zz = full.reshape(C, ldzz).T[:R, :] if R * C else np.zeros((R, C))
+                if ldzz > R and C > 0:   # padding rows untouched
+                    pad = t[: ldzz * C].view(C, ldzz)[:, R:]
+                    assert bool(torch.isnan(pad.float()).all()), "write into ld padding"
+                result["Z"] = zz
+            elif kindk == "s":
+                check_canary(t, 1)
+                result["s"] = from_device(t[:1], "f64")[0]
+            else:
+                nv = C if name == "schur_colsum" else R
+                check_canary(t, nv)
+                result["v"] = from_device(t[:nv], "f64")
+        result["_launches"] = launches
+        return result
+    finally:
+        fx.fx_expr_destroy(h)
+
+
+# ---------------------------------------------------------------- comparison
+
+def scaled_error(gpu, ref, sigma, storage):
+    """(max scaled error, #expected overflows, #bad non-finite, max plain rel)."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    sigma = np.broadcast_to(np.asarray(sigma, dtype=np.float64), ref.shape)
+    over = np.abs(ref) > MAXFIN[storage]
+    bad = 0
+    if np.any(over):
+        okinf = np.isinf(gpu[over]) & (np.sign(gpu[over]) == np.sign(ref[over]))
+        # a finite result is acceptable only when it is the largest finite value (rounding edge)
+        okmax = np.abs(gpu[over]) == MAXFIN[storage]
+        bad += int(np.sum(~(okinf | okmax)))
+    fin = ~over
+    g, r, s = gpu[fin], ref[fin], sigma[fin]
+    bad += int(np.sum(~np.isfinite(g)))
+    g = np.where(np.isfinite(g), g, np.inf)
+    denom = np.maximum(np.maximum(s, np.abs(r)), TINY[storage])
+    err = np.abs(g - r) / denom
+    if storage == "f16":
+        # outputs below the FP16 normal range: absolute bound of one subnormal step
+        sub = np.abs(r) < 2.0**-14
+        bad += int(np.sum(np.abs(g[sub] - r[sub]) > 2.0**-24))
+        err = np.where(sub, 0.0, err)
+    nz = np.abs(r) > TINY[storage]
+    rel = float(np.max(np.abs(g[nz] - r[nz]) / np.abs(r[nz]))) if np.any(nz) else 0.0
+    return (float(np.max(err)) if err.size else 0.0), int(np.sum(over)), bad, rel
+
+
+def oracle_outputs(name, env, scalars=None, sample=None):
+    """Oracle values and sigma: full matrices, or at `sample` = (R, C) index arrays."""
+    tree = tree_of(name, scalars)
+    if name == "schur_trans_accu":
+        if sample is None:
+            z, sz = oracle.evaluate_sigma(tree, env)
+            res = {"Z": (z, sz)}
+        else:
+            res = {"Z": oracle.at_sigma(tree, env, *sample)}
+        s, ss = oracle.evaluate_sigma(f"(accu {tree})", env)
+        res["s"] = (s[0, 0], ss[0, 0])
+        return res
+    root = oracle.parse(tree)
+    if root.op in oracle.REDUCTIONS:
+        v, sv = oracle.evaluate_sigma(tree, env)
+        if root.op in ("accu", "norm"):
+            return {"s": (v[0, 0], sv[0, 0])}
+        return {"v": (v.ravel(), sv.ravel())}
+    if sample is None:
+        return {"Z": oracle.evaluate_sigma(tree, env)}
+    return {"Z": oracle.at_sigma(tree, env, *sample)}

@@ -1,0 +1,139 @@
+"""The C ABI library loads, exports every declared entry point, and checks
+its arguments on the host (no GPU needed: none of these calls reach CUDA)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+EXPECTED = {
+    "schur_exp_trans": (4, 1, 1, "elementwise"),
+    "sqdiff_accu": (2, 1, 0, "full_reduce"),
+    "schur_sqrt_sigmoid": (4, 1, 1, "elementwise"),
+    "schur_colsum": (2, 1, 0, "dim_reduce"),
+    "absdiff_rowmax": (2, 1, 0, "dim_reduce"),
+    "diff_norm": (2, 1, 0, "full_reduce"),
+    "schur_trans_accu": (3, 2, 1, "multi"),
+    "sigmoid_sqloss": (4, 1, 0, "full_reduce"),
+}
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "fx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fx_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(fxlib):
+    names = declared_functions()
+    assert len(names) >= 19
+    L = ctypes.CDLL(fxlib.lib_path)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_registry_lists_expected_trees(fxlib):
+    listed = {(n, d) for n, d, _ in fxlib.fx_list()}
+    for name in EXPECTED:
+        for d in (fxlib.FX_F32, fxlib.FX_F64, fxlib.FX_BF16, fxlib.FX_F16):
+            assert (name, d) in listed, (name, d)
+
+
+@pytest.mark.parametrize("name", sorted(EXPECTED))
+def test_info_and_slots(fxlib, name):
+    h = fxlib.fx_expr_create(name, fxlib.FX_F32)
+    try:
+        assert fxlib.fx_expr_info(h) == EXPECTED[name]
+        n_in, n_out = EXPECTED[name][:2]
+        names = [fxlib.fx_expr_slot_name(h, k) for k in range(n_in + n_out)]
+        assert len(set(names)) == n_in + n_out
+        with pytest.raises(fxlib.FxError):
+            fxlib.fx_expr_slot_name(h, n_in + n_out)
+    finally:
+        fxlib.fx_expr_destroy(h)
+
+
+def test_create_errors(fxlib):
+    with pytest.raises(fxlib.FxError) as e:
+        fxlib.fx_expr_create("no_such_tree", fxlib.FX_F32)
+    assert e.value.status == -9
+    with pytest.raises(fxlib.FxError) as e:
+        fxlib.fx_expr_create("schur_exp_trans", 7)
+    assert e.value.status == -1
+
+
+def test_bind_checks(fxlib):
+    h = fxlib.fx_expr_create("schur_exp_trans", fxlib.FX_F32)
+    try:
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_expr_bind(h, 9, 0x1000, 4, 4, 4)
+        assert e.value.status == -1
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_expr_bind(h, 0, 0x1000, 8, 4, 4)          # ld < rows
+        assert e.value.status == -1
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_expr_bind(h, 0, 0x1002, 4, 4, 4)          # not 4-byte aligned
+        assert e.value.status == -4
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_expr_bind(h, 0, 0, 4, 4, 4)               # null, non-empty
+        assert e.value.status == -1
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_expr_bind(h, 0, 0x1000, -1, 4, 4)
+        assert e.value.status == -2
+        fxlib.fx_expr_bind(h, 0, 0, 0, 0, 1)                   # empty is fine
+    finally:
+        fxlib.fx_expr_destroy(h)
+
+
+def test_unbound_and_shape_errors_before_any_launch(fxlib):
+    h = fxlib.fx_expr_create("schur_exp_trans", fxlib.FX_F32)
+    try:
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_eval(h)
+        assert e.value.status == -5
+        for k in range(3):
+            fxlib.fx_expr_bind(h, k, 0x1000, 8, 6, 8)
+        fxlib.fx_expr_bind(h, 3, 0x1000, 8, 6, 8)            # D must be 6 x 8
+        fxlib.fx_expr_bind(h, 4, 0x1000, 8, 6, 8)
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_eval(h)
+        assert e.value.status == -2
+        assert "slot 3" in fxlib.fx_last_error_string()
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_eval_backward(h, 0, [0] * 4)
+        assert e.value.status == -6
+    finally:
+        fxlib.fx_expr_destroy(h)
+
+
+def test_reduction_output_shape_checked(fxlib):
+    h = fxlib.fx_expr_create("schur_colsum", fxlib.FX_F64)
+    try:
+        fxlib.fx_expr_bind(h, 0, 0x1000, 8, 6, 8)
+        fxlib.fx_expr_bind(h, 1, 0x1000, 8, 6, 8)
+        fxlib.fx_expr_bind(h, 2, 0x1000, 8, 1, 8)            # colsum is 1 x 6
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_eval(h)
+        assert e.value.status == -2
+    finally:
+        fxlib.fx_expr_destroy(h)
+
+
+def test_scalars(fxlib):
+    h = fxlib.fx_expr_create("schur_exp_trans", fxlib.FX_BF16)
+    try:
+        assert fxlib.fx_expr_get_scalar(h, 0) == 3.5
+        fxlib.fx_expr_set_scalar(h, 0, -1.25)
+        assert fxlib.fx_expr_get_scalar(h, 0) == -1.25
+        with pytest.raises(fxlib.FxError):
+            fxlib.fx_expr_set_scalar(h, 1, 0.0)
+    finally:
+        fxlib.fx_expr_destroy(h)
+
+
+def test_status_strings(fxlib):
+    for s in range(0, -10, -1):
+        assert fxlib.fx_status_string(s)
+    fxlib.fx_expr_destroy(None)

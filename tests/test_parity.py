@@ -1,0 +1,156 @@
+"""Parity of the fused CUDA path with the FP64 oracle (GPU).
+
+Small and ragged shapes are compared element by element; the full-size
+workloads (1024^2 FP32, 8192^2 FP32/FP64, 16384^2 BF16/FP16) on all
+reductions and on a seeded sample of element-wise outputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from harness import (SLOTS, oracle_outputs, run, scaled_error, specs_for, tolerance, tree_of)
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["schur_exp_trans", "sqdiff_accu", "schur_sqrt_sigmoid", "schur_colsum",
+         "absdiff_rowmax", "diff_norm", "schur_trans_accu", "sigmoid_sqloss"]
+DIST = {"schur_exp_trans": "uniform", "sqdiff_accu": "uniform", "schur_trans_accu": "uniform",
+        "sigmoid_sqloss": "normal_half"}
+SMALL = [(1, 1), (1, 7), (7, 1), (33, 17), (100, 37), (257, 129), (64, 64)]
+
+
+@pytest.fixture(scope="module")
+def fx(fxlib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return fxlib
+
+
+def check(name, storage, got, ref, label=""):
+    for key, (rv, rs) in ref.items():
+        tol = tolerance(name, storage, key)
+        # reductions are stored in FP32 (FP64 for f64)
+        st = storage if key == "Z" else ("f64" if storage == "f64" else "f32")
+        err, nover, bad, rel = scaled_error(got[key], rv, rs, st)
+        assert bad == 0, f"{name}/{storage}/{key}{label}: {bad} wrong non-finite outputs"
+        assert err <= tol, f"{name}/{storage}/{key}{label}: scaled error {err:.3e} > {tol:.1e}"
+
+
+def env_for(name, storage, R, C, seed=7, lds=None):
+    return synth.operands(seed, specs_for(name, R, C), storage, DIST.get(name, "normal"), lds=lds)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
+@pytest.mark.parametrize("name", NAMES)
+def test_small_shapes(fx, name, storage):
+    for R, C in SMALL:
+        env = env_for(name, storage, R, C)
+        got = run(fx, name, storage, env, R, C)
+        check(name, storage, got, oracle_outputs(name, env), f" at {R}x{C}")
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("name", NAMES)
+def test_leading_dimension_and_misalignment(fx, name, storage):
+    R, C = 45, 23
+    lds = {s: (c_rows + 3) for s, c_rows, _ in specs_for(name, R, C)}
+    env = env_for(name, storage, R, C, seed=11, lds=lds)
+    ref = oracle_outputs(name, env)
+    check(name, storage, run(fx, name, storage, env, R, C, ldz=R + 5), ref, " (ld > rows)")
+    env2 = env_for(name, storage, R, C, seed=12)
+    ref2 = oracle_outputs(name, env2)
+    check(name, storage, run(fx, name, storage, env2, R, C, offset=1), ref2, " (misaligned base)")
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("name", NAMES)
+def test_unfused_baseline_matches(fx, name, storage):
+    R, C = 96, 80
+    env = env_for(name, storage, R, C, seed=13)
+    got = run(fx, name, storage, env, R, C, unfused=True)
+    check(name, storage, got, oracle_outputs(name, env), " (unfused)")
+    assert got["_launches"] >= 2
+
+
+@pytest.mark.parametrize("name", ["sqdiff_accu", "schur_colsum", "absdiff_rowmax", "diff_norm",
+                                  "schur_trans_accu", "sigmoid_sqloss"])
+def test_reductions_bitwise_repeatable(fx, name):
+    R, C = 1000, 700
+    env = env_for(name, "f32", R, C, seed=14)
+    a = run(fx, name, "f32", env, R, C)
+    b = run(fx, name, "f32", env, R, C)
+    for k in a:
+        if k != "_launches":
+            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+
+
+def test_one_launch_per_fused_tree(fx):
+    for name in NAMES:
+        env = env_for(name, "f32", 300, 200)
+        assert run(fx, name, "f32", env, 300, 200)["_launches"] == 1, name
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_empty_shapes(fx, name):
+    for R, C in [(0, 5), (5, 0), (0, 0)]:
+        env = env_for(name, "f32", R, C)
+        got = run(fx, name, "f32", env, R, C)
+        if "s" in got:
+            assert got["s"] == 0.0
+        if "v" in got:
+            if name == "absdiff_rowmax":
+                assert np.all(got["v"] == -np.inf)
+            else:
+                assert np.all(got["v"] == 0.0)
+
+
+def test_scalar_override(fx):
+    R, C = 50, 40
+    env = env_for("schur_exp_trans", "f32", R, C)
+    got = run(fx, "schur_exp_trans", "f32", env, R, C, scalars=[-0.75])
+    check("schur_exp_trans", "f32", got, oracle_outputs("schur_exp_trans", env, [-0.75]))
+
+
+# ---------------------------------------------------------------- full-size workloads
+
+def _sampled_check(fx, name, storage, env, R, C, n_sample=1 << 18, seed=99):
+    got = run(fx, name, storage, env, R, C)
+    rng = np.random.default_rng(seed)
+    rr = rng.integers(0, R, n_sample)
+    cc = rng.integers(0, C, n_sample)
+    ref = {}
+    full = oracle_outputs(name, env, sample=(rr, cc)) if "Z" in got else oracle_outputs(name, env)
+    for k, v in full.items():
+        ref[k] = v
+    if "Z" in got:
+        got = dict(got)
+        got["Z"] = got["Z"][rr, cc]
+    check(name, storage, got, ref, f" at {R}x{C}")
+
+
+def test_workload_1024_f32(fx):
+    R = C = 1024
+    env = synth.operands(0, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], "f32", "uniform")
+    for name in ("schur_exp_trans", "sqdiff_accu"):
+        got = run(fx, name, "f32", env, R, C)
+        check(name, "f32", got, oracle_outputs(name, env), " at 1024^2")
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_workload_8192(fx, storage):
+    R = C = 8192
+    env = synth.operands(1, [("X", R, C), ("Y", R, C), ("W", R, C), ("V", R, C)], storage,
+                         "normal")
+    for name in ("schur_sqrt_sigmoid", "schur_colsum", "absdiff_rowmax", "diff_norm"):
+        _sampled_check(fx, name, storage, env, R, C)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_workload_16384(fx, storage):
+    R = C = 16384
+    env = synth.operands(2, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], storage,
+                         "lognormal_signed")
+    for name in ("schur_exp_trans", "sqdiff_accu"):
+        _sampled_check(fx, name, storage, env, R, C)
