@@ -188,6 +188,37 @@ fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* b
  * enqueued (for launch accounting). */
 int fx_expr_last_launches(const fx_expr* x);
 
+/* ---- evaluation without device allocation ------------------------------ */
+
+/* Bytes of the fixed device array behind fx_sqdiff_accu_f32_noalloc: room
+ * for 4096 per-block partial sums (16 bytes each) and a completion ticket. */
+#define FX_NOALLOC_SCRATCH (4096 * 16 + 256)
+
+/* s = accu(square(A - B)) for FP32 matrices A and B (rows x cols,
+ * column-major, leading dimension ld, device pointers), written to the
+ * device float *s. Same kernel, launch plan and result as fx_eval on
+ * "sqdiff_accu" with f32 storage, but this call allocates no device memory
+ * and needs no fx_expr object. The paper has no counterpart: it is for
+ * callers that cannot call cudaMalloc while they compute - code working
+ * inside a device-memory budget fixed in advance, code that must not add
+ * the device synchronisation cudaMalloc/cudaFree can cause, or a host whose
+ * allocator belongs to another framework.
+ *  - Scratch: a file-scope device array of FX_NOALLOC_SCRATCH bytes, held
+ *    by every GPU that loads the library until the process exits.
+ *  - The first call on each device looks up that array's device address
+ *    (cudaGetSymbolAddress) with the device current; make that first call
+ *    before any stream capture on the device.
+ *  - Every call on a device shares the one array, which keeps what the last
+ *    call left; the call clears the part that must start at zero. Calls
+ *    whose kernels overlap on the GPU (different streams, no ordering) race
+ *    on it: order them on one stream or with events.
+ *  - FX_E_UNSUPPORTED if the launch would need more than 4096 partial sums
+ *    (a 152-SM GB300 at the default launch shape needs at most 1216);
+ *    FX_E_ARG / FX_E_SHAPE / FX_E_ALIGN as for fx_expr_bind (4-byte
+ *    alignment); FX_E_CUDA if a CUDA call fails. Asynchronous on `stream`. */
+fx_status fx_sqdiff_accu_f32_noalloc(const float* A, const float* B, int64_t rows, int64_t cols,
+                                     int64_t ld, float* s, void* stream);
+
 /* ---- errors ------------------------------------------------------------- */
 
 const char* fx_last_error_string(void);
