@@ -1,28 +1,40 @@
-"""Benchmark: fused evaluation of the 8192 x 8192 FP32 expression workload.
+"""Benchmark of fused expression evaluation on one GB300 (or N replicas).
 
-One step evaluates, on four 8192 x 8192 column-major FP32 matrices X, Y, W,
-V drawn i.i.d. N(0, 1) (seed 1):
+Default workload (the JSON line the driver reads): one step evaluates, on
+four 8192 x 8192 column-major FP32 matrices X, Y, W, V drawn i.i.d. N(0, 1)
+(seed 1),
     Z      = X % Y + sqrt(abs(W)) / (1 + exp(-V))
     colsum = sum(X % Y, 0)
     rowmax = max(abs(X - Y), 1)
     nrm    = norm(X - Y, 2)
-each as one fused kernel. The metric is the effective HBM bandwidth:
+each as one fused kernel. The metric is effective HBM bandwidth:
 algorithmic bytes (every input element read once, every output written
-once) per second. Inputs (256 MiB each) are larger than L2, so no flush is
-needed between iterations.
+once) per second. The inputs (256 MiB each) are larger than L2, so there is
+no flush between iterations.
 
---gpus N runs N independent replicas (one process per GPU, launched by
-torch.distributed.run); value = bytes of all ranks / max elapsed time.
---impl reference times the FP64 CPU oracle on a bounded sample instead.
+--workload selects the other measured configurations (same JSON fields):
+  expr8192_f64   the default trees with FP64 storage
+  small1024      Z = A%B + 3.5*exp(C) - trans(D) and s = accu(square(A-B)),
+                 FP32 1024^2 (L2 flushed before every kernel, device-timed)
+  prec16384_bf16 / prec16384_f16   the 1024^2 trees at 16384^2
+  batch4096      Z = A%B + 0.5*trans(C), s = accu(Z) over 4096 matrices,
+                 rows/cols log-uniform in [16, 2048], one graph-replayed launch
+  loss8192_f32 / loss8192_bf16     L = accu(square(sigmoid(X%W + b) - Y))
+                 forward and fused backward (dX, dW, db)
+
+--gpus N: N independent replicas (one process per GPU, torch.distributed.run);
+value = bytes of all ranks / max elapsed time over ranks.
+--impl reference: the FP64 CPU oracle, timed on a bounded sample of the
+workload per step.
 """
 from __future__ import annotations
 
 import argparse
 import csv
+import datetime as dt
 import hashlib
 import io
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -33,10 +45,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fused-expr effective HBM GB/s (% of GB300 peak) and speedup vs unfused per-op"
-WORKLOAD = "X%Y+sqrt(abs(W))/(1+exp(-V)), sum(X%Y,0), max(abs(X-Y),1), norm(X-Y,2) at 8192x8192"
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture, valid
-# only while the kernel source hashes to the recorded value.
+# DRAM traffic per launch of a dominant kernel from an ncu capture (bytes),
+# valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {}
 
 
@@ -48,27 +59,260 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_peaks():
+def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+            return float(json.load(f)["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
 
-def alg_bytes(R, C, es, rs):
-    """Algorithmic bytes of one step: inputs read once, outputs written once."""
-    N = R * C
-    z = 5 * N * es                  # X, Y, W, V in; Z out
-    colsum = 2 * N * es + C * rs
-    rowmax = 2 * N * es + R * rs
-    nrm = 2 * N * es + rs
-    return {"Z": z, "colsum": colsum, "rowmax": rowmax, "nrm": nrm}
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons; keeps the samples
+    whose timestamps fall inside [t0, t1] (host wall clock)."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.p = index, None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self, t0, t1):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
+        for r in csv.reader(io.StringIO(out)):
+            if len(r) < 10:
+                continue
+            try:
+                ts = dt.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(r[2]), float(r[3]), float(r[4]),
+                             [r[6 + k].strip().lower() == "active" for k in range(4)]))
+            except ValueError:
+                continue
+        inside = [x for x in rows if t0 - 0.05 <= x[0] <= t1 + 0.05] or rows
+        reasons = sorted({names[k] for x in inside for k in range(4) if x[4][k]})
+        return {"sm_mhz": statistics.median(x[1] for x in inside) if inside else None,
+                "sm_max_mhz": max((x[2] for x in inside), default=None),
+                "power_w_max": max((x[3] for x in inside), default=None),
+                "reasons": reasons, "samples": len(inside)}
 
 
-TREES = [("schur_sqrt_sigmoid", "Z"), ("schur_colsum", "colsum"), ("absdiff_rowmax", "rowmax"),
-         ("diff_norm", "nrm")]
+# ---------------------------------------------------------------- workloads
+
+class Op:
+    """One fused evaluation: a launch, its unfused twin, and its algorithmic bytes."""
+
+    def __init__(self, key, nbytes, launch, unfused=None, launches=None):
+        self.key, self.bytes, self.launch, self.unfused, self.launches = (
+            key, nbytes, launch, unfused, launches)
+
+
+def _bind(fx, h, k, t, rows, cols, ld):
+    fx.fx_expr_bind(h, k, t.data_ptr(), rows, cols, ld)
+
+
+def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
+    """Ops for single-matrix trees. trees: [(name, key, input names, out kind)]."""
+    import numpy as np
+    code = {"f32": fx.FX_F32, "f64": fx.FX_F64, "bf16": fx.FX_BF16, "f16": fx.FX_F16}[storage]
+    tdt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16,
+           "f16": torch.float16}[storage]
+    rdt = torch.float64 if storage == "f64" else torch.float32
+    es = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[storage]
+    rs = 8 if storage == "f64" else 4
+    d = {}
+    for k, b in env.items():
+        if storage == "bf16":
+            t = torch.from_numpy(b.data.view(np.int16)).view(torch.bfloat16)
+        else:
+            t = torch.from_numpy(b.data)
+        d[k] = t.to(dev)
+    keep["inputs"] = d
+    ops = []
+    for name, key, ins, kind in trees:
+        h = fx.fx_expr_create(name, code)
+        nb = 0
+        for k, s in enumerate(ins):
+            b = env[s]
+            _bind(fx, h, k, d[s], b.rows, b.cols, b.ld)
+            nb += b.rows * b.cols * es
+        if kind == "Z":
+            o = torch.empty(R * C, dtype=tdt, device=dev)
+            _bind(fx, h, len(ins), o, R, C, R)
+            nb += R * C * es
+        elif kind == "s":
+            o = torch.empty(1, dtype=rdt, device=dev)
+            _bind(fx, h, len(ins), o, 1, 1, 1)
+            nb += rs
+        elif kind == "col":
+            o = torch.empty(C, dtype=rdt, device=dev)
+            _bind(fx, h, len(ins), o, 1, C, 1)
+            nb += C * rs
+        elif kind == "row":
+            o = torch.empty(R, dtype=rdt, device=dev)
+            _bind(fx, h, len(ins), o, R, 1, R)
+            nb += R * rs
+        keep[key] = (h, o)
+        ops.append(Op(key, nb, (lambda h=h: fx.fx_eval(h, sp)),
+                      (lambda h=h: fx.fx_eval_unfused(h, sp)),
+                      (lambda h=h: fx.fx_expr_last_launches(h))))
+    return ops
+
+
+def workload(name, fx, torch, dev, sp, keep, size=8192):
+    """(ops, config dict, dominant op key, flush_l2, dtype) for a workload."""
+    import numpy as np
+    import synth
+    if name in ("expr8192", "expr8192_f64"):
+        storage = "f64" if name.endswith("f64") else "f32"
+        R = C = size
+        env = synth.operands(1, [("X", R, C), ("Y", R, C), ("W", R, C), ("V", R, C)], storage,
+                             "normal")
+        trees = [("schur_sqrt_sigmoid", "Z", "XYWV", "Z"), ("schur_colsum", "colsum", "XY", "col"),
+                 ("absdiff_rowmax", "rowmax", "XY", "row"), ("diff_norm", "nrm", "XY", "s")]
+        cfg = {"workload": "X%Y+sqrt(abs(W))/(1+exp(-V)), sum(X%Y,0), max(abs(X-Y),1), "
+                           f"norm(X-Y,2) at {R}x{C}", "rows": R, "cols": C,
+               "inputs": "X,Y,W,V i.i.d. N(0,1), seed 1, column-major",
+               "l2": "inputs larger than L2 (256 MiB each in FP32), no flush"}
+        keep["env"] = env
+        return _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep), cfg, "Z", False, storage
+    if name in ("small1024", "prec16384_bf16", "prec16384_f16"):
+        storage = "f32" if name == "small1024" else name.split("_")[1]
+        R = C = 1024 if name == "small1024" else 16384
+        dist = "uniform" if name == "small1024" else "lognormal_signed"
+        env = synth.operands(0, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], storage, dist)
+        trees = [("schur_exp_trans", "Z", "ABCD", "Z"), ("sqdiff_accu", "s", "AB", "s")]
+        cfg = {"workload": f"A%B+3.5*exp(C)-trans(D) and accu(square(A-B)) at {R}x{C}",
+               "rows": R, "cols": C, "inputs": f"A,B,C,D {dist}, seed 0, column-major",
+               "l2": "L2 flushed before every kernel (256 MiB write), device-timed per kernel"
+               if name == "small1024" else "inputs larger than L2, no flush"}
+        return (_expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep), cfg, "Z",
+                name == "small1024", storage)
+    if name == "batch4096":
+        return batch_workload(fx, torch, dev, sp, keep)
+    if name in ("loss8192_f32", "loss8192_bf16"):
+        return loss_workload(fx, torch, dev, sp, keep, name.split("_")[1])
+    raise SystemExit(f"unknown workload {name}")
+
+
+def batch_workload(fx, torch, dev, sp, keep):
+    import numpy as np
+    import synth
+    rows, cols, ops_ = synth.batch_operands(2, 4096, [("A", False), ("B", False), ("C", True)])
+    n = len(rows)
+
+    def arena(mats):
+        offs, pos = [], 0
+        for m in mats:
+            offs.append(pos)
+            pos += (m.data.size + 3) // 4 * 4
+        host = np.zeros(pos, dtype=np.float32)
+        for m, o in zip(mats, offs):
+            host[o:o + m.data.size] = m.data
+        return torch.from_numpy(host).to(dev), offs
+
+    A, oa = arena(ops_["A"])
+    B, ob = arena(ops_["B"])
+    Cm, oc = arena(ops_["C"])
+    del ops_
+    oz, pos = [], 0
+    for r, c in zip(rows, cols):
+        oz.append(pos)
+        pos += (int(r * c) + 3) // 4 * 4
+    Z = torch.empty(pos, dtype=torch.float32, device=dev)
+    S = torch.empty(n, dtype=torch.float32, device=dev)
+    items = (fx.BatchItem * n)()
+    for i in range(n):
+        it = items[i]
+        it.ptr[0] = A.data_ptr() + 4 * oa[i]
+        it.ptr[1] = B.data_ptr() + 4 * ob[i]
+        it.ptr[2] = Cm.data_ptr() + 4 * oc[i]
+        it.ptr[3] = Z.data_ptr() + 4 * oz[i]
+        it.ptr[4] = S.data_ptr() + 4 * i
+        it.rows, it.cols = int(rows[i]), int(cols[i])
+    h = fx.fx_expr_create("schur_trans_accu", fx.FX_F32)
+    keep["batch"] = (A, B, Cm, Z, S, items, h)
+    nel = int(np.sum(rows * cols))
+    nbytes = 16 * nel + 4 * n
+    # unfused and unbatched baseline: the same tree one operator per launch, matrix by matrix
+    per = []
+    for i in range(n):
+        e = fx.fx_expr_create("schur_trans_accu", fx.FX_F32)
+        r, c = int(rows[i]), int(cols[i])
+        fx.fx_expr_bind(e, 0, items[i].ptr[0], r, c, r)
+        fx.fx_expr_bind(e, 1, items[i].ptr[1], r, c, r)
+        fx.fx_expr_bind(e, 2, items[i].ptr[2], c, r, c)
+        fx.fx_expr_bind(e, 3, items[i].ptr[3], r, c, r)
+        fx.fx_expr_bind(e, 4, items[i].ptr[4], 1, 1, 1)
+        per.append(e)
+    keep["per"] = per
+
+    def unfused():
+        for e in per:
+            fx.fx_eval_unfused(e, sp)
+
+    op = Op("batch", nbytes, lambda: fx.fx_eval_batch(h, items, sp, True), unfused,
+            lambda: fx.fx_expr_last_launches(h))
+    cfg = {"workload": "Z=A%B+0.5*trans(C), s=accu(Z) over 4096 matrices, rows/cols "
+                       "log-uniform [16,2048] seed 2", "matrices": n, "elements": nel,
+           "l2": "working set 11.5 GB, no flush", "graph": True}
+    return [op], cfg, "batch", False, "f32"
+
+
+def loss_workload(fx, torch, dev, sp, keep, storage):
+    import numpy as np
+    import synth
+    R = C = 8192
+    env = synth.operands(3, [("X", R, C), ("W", R, C), ("Y", R, C), ("b", R, 1)], storage,
+                         "normal_half")
+    tdt = torch.float32 if storage == "f32" else torch.bfloat16
+    es = 4 if storage == "f32" else 2
+    d = {}
+    for k, b in env.items():
+        t = torch.from_numpy(b.data.view(np.int16)).view(torch.bfloat16) if storage == "bf16" \
+            else torch.from_numpy(b.data)
+        d[k] = t.to(dev)
+    code = fx.FX_F32 if storage == "f32" else fx.FX_BF16
+    h = fx.fx_expr_create("sigmoid_sqloss", code)
+    for k, s in enumerate("XWYb"):
+        b = env[s]
+        fx.fx_expr_bind(h, k, d[s].data_ptr(), b.rows, b.cols, b.ld)
+    L = torch.empty(1, dtype=torch.float32, device=dev)
+    fx.fx_expr_bind(h, 4, L.data_ptr(), 1, 1, 1)
+    g = {s: torch.empty(R * C, dtype=tdt, device=dev) for s in "XW"}
+    g["b"] = torch.empty(R, dtype=tdt, device=dev)
+    ptrs = [g["X"].data_ptr(), g["W"].data_ptr(), 0, g["b"].data_ptr()]
+    keep["loss"] = (d, L, g, h)
+    fwd_bytes = 3 * R * C * es + R * es + 4
+    bwd_bytes = 3 * R * C * es + R * es + 2 * R * C * es + R * es
+    ops = [Op("forward", fwd_bytes, lambda: fx.fx_eval(h, sp), lambda: fx.fx_eval_unfused(h, sp),
+              lambda: fx.fx_expr_last_launches(h)),
+           Op("backward", bwd_bytes, lambda: fx.fx_eval_backward(h, 0, ptrs, sp), None,
+              lambda: fx.fx_expr_last_launches(h))]
+    cfg = {"workload": f"L=accu(square(sigmoid(X%W+b.each_col)-Y)) forward and backward (dX,dW,db), "
+                       f"8192x8192 {storage}", "rows": R, "cols": C,
+           "inputs": "X,W,Y,b N(0, sd 0.5), seed 3", "l2": "inputs larger than L2, no flush"}
+    return ops, cfg, "backward", False, storage
+
+
+# ---------------------------------------------------------------- CPU oracle
+
 ORACLE_TREES = {
     "Z": "(+ (% X Y) (/ (sqrt (abs W)) (+ 1.0 (exp (neg V)))))",
     "colsum": "(sum (% X Y) 0)",
@@ -77,96 +321,53 @@ ORACLE_TREES = {
 }
 
 
-class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
-
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, index):
-        self.index = index
-        self.p = None
-
-    def start(self):
-        try:
-            self.p = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.p = None
-
-    def stop(self):
-        if not self.p:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        out, _ = self.p.communicate(timeout=10)
-        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in rows:
-            for k, nm in enumerate(names):
-                if r[5 + k].strip().lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
-
-
-def make_inputs(R, C, storage, seed=1):
-    import synth
-    return synth.operands(seed, [("X", R, C), ("Y", R, C), ("W", R, C), ("V", R, C)], storage,
-                          "normal")
-
-
-def cpu_oracle_time(R, C, cols, storage):
-    """Oracle on the first `cols` columns of the workload: (seconds, bytes)."""
+def cpu_oracle_time(R, cols, storage):
+    """The oracle on an R x cols panel of the default workload: (s, bytes)."""
     import oracle
-    env = make_inputs(R, cols, storage)
+    import synth
+    env = synth.operands(1, [("X", R, cols), ("Y", R, cols), ("W", R, cols), ("V", R, cols)],
+                         storage, "normal")
     es = 8 if storage == "f64" else 4
-    b = alg_bytes(R, cols, es, es)
+    N = R * cols
+    nbytes = 5 * N * es + (2 * N * es + cols * es) + (2 * N * es + R * es) + (2 * N * es + es)
     t0 = time.perf_counter()
-    for _, key in TREES:
-        oracle.evaluate(ORACLE_TREES[key], env)
-    return time.perf_counter() - t0, sum(b.values())
+    for tree in ORACLE_TREES.values():
+        oracle.evaluate(tree, env)
+    return time.perf_counter() - t0, nbytes
 
 
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle timed on a bounded sample of the workload per step."""
     if rank != 0:
         return
-    R = args.size
-    cols = args.ref_cols
+    R, cols = 8192, args.ref_cols
     for _ in range(args.warmup):
-        cpu_oracle_time(R, cols, cols, args.dtype)
-    tot_t, tot_b = 0.0, 0
+        cpu_oracle_time(R, cols, "f32")
+    tt, tb = 0.0, 0
     for _ in range(args.steps):
-        t, b = cpu_oracle_time(R, cols, cols, args.dtype)
-        tot_t += t
-        tot_b += b
-    v = tot_b / tot_t / 1e9
-    line = {
+        t, b = cpu_oracle_time(R, cols, "f32")
+        tt += t
+        tb += b
+    v = tb / tt / 1e9
+    sample = (f"{R}x{cols} column panel of X,Y,W,V per step, all four trees, FP64 numpy "
+              "tree walker, one thread")
+    print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(1000 * tot_t / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rows": R, "cols": R, "sample_cols": cols,
-                   "l2": "inputs larger than L2"},
+        "ms_per_step": round(1000 * tt / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "X%Y+sqrt(abs(W))/(1+exp(-V)), sum(X%Y,0), max(abs(X-Y),1), "
+                               "norm(X-Y,2) at 8192x8192", "sample_cols": cols,
+                   "l2": "CPU run, no GPU"},
         "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{R}x{cols} column panel of each input per step, FP64 "
-                                   "numpy tree walker, single thread"},
+                         "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
-        "gpu_launches": 0,
-    }
-    print(json.dumps(line), flush=True)
+        "gpu_launches": 0}), flush=True)
 
+
+# ---------------------------------------------------------------- GPU run
 
 def run_ours(args, rank, world):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -175,175 +376,179 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    R = C = args.size
-    storage = args.dtype
-    code = {"f32": fx.FX_F32, "f64": fx.FX_F64}[storage]
-    es = 8 if storage == "f64" else 4
-    tdt = torch.float64 if storage == "f64" else torch.float32
-    env = make_inputs(R, C, storage)
-    host = {k: torch.from_numpy(v.data).pin_memory() for k, v in env.items()}
-    d = {k: v.to(dev) for k, v in host.items()}
-    Z = torch.empty(R * C, dtype=tdt, device=dev)
-    outs = {"Z": Z, "colsum": torch.empty(C, dtype=tdt, device=dev),
-            "rowmax": torch.empty(R, dtype=tdt, device=dev),
-            "nrm": torch.empty(1, dtype=tdt, device=dev)}
-    shapes = {"Z": (R, C, R), "colsum": (1, C, 1), "rowmax": (R, 1, R), "nrm": (1, 1, 1)}
-    inputs = {"schur_sqrt_sigmoid": "XYWV", "schur_colsum": "XY", "absdiff_rowmax": "XY",
-              "diff_norm": "XY"}
     stream = torch.cuda.Stream(device=dev)
     sp = int(stream.cuda_stream)
-    ex = {}
-    for name, key in TREES:
-        h = fx.fx_expr_create(name, code)
-        for k, s in enumerate(inputs[name]):
-            fx.fx_expr_bind(h, k, d[s].data_ptr(), R, C, R)
-        r, c, ld = shapes[key]
-        fx.fx_expr_bind(h, len(inputs[name]), outs[key].data_ptr(), r, c, ld)
-        if args.tune:
-            fx.fx_tune(h, "search", sp)
-        ex[key] = h
+    keep = {}
+    ops, cfg, dom, flush, storage = workload(args.workload, fx, torch, dev, sp, keep, args.size)
+    if args.tune:
+        for key, val in keep.items():
+            if isinstance(val, tuple) and len(val) == 2 and key in [o.key for o in ops]:
+                fx.fx_tune(val[0], "search", sp)
+    flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
     torch.cuda.synchronize()
-    bytes_ = alg_bytes(R, C, es, es)
-    step_bytes = sum(bytes_.values())
+    step_bytes = sum(o.bytes for o in ops)
+    K = args.steps
 
-    ev_z = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in range(args.steps)]
-
-    def step(i=None, unfused=False):
-        launches = 0
-        for name, key in TREES:
-            h = ex[key]
-            if i is not None and key == "Z":
-                ev_z[i][0].record(stream)
-            (fx.fx_eval_unfused if unfused else fx.fx_eval)(h, sp)
-            if i is not None and key == "Z":
-                ev_z[i][1].record(stream)
-            launches += fx.fx_expr_last_launches(h)
-        return launches
+    def fl():
+        if flush_buf is not None:
+            flush_buf.zero_()
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step()
+            for o in ops:
+                fl()
+                o.launch()
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        ev = {o.key: [] for o in ops}
         clk = Clocks(local)
         clk.start()
-        time.sleep(0.3)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        t0.record(stream)
-        launches = 0
-        for i in range(args.steps):
-            launches += step(i)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        clocks = clk.stop()
+        time.sleep(0.4)
         if world > 1:
             dist.barrier()
+        torch.cuda.synchronize()
+        t_start = time.time()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        launches = 0
+        for i in range(K):
+            for o in ops:
+                fl()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                o.launch()
+                b.record(stream)
+                ev[o.key].append((a, b))
+                launches += o.launches() if o.launches else 1
+        t1.record(stream)
+        torch.cuda.synchronize()
+        t_end = time.time()
+        if world > 1:
+            dist.barrier()
+        clocks = clk.stop(t_start, t_end)
+        per_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
         ms = t0.elapsed_time(t1)
-        z_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_z)
+        if flush:   # device time of the kernels alone (flushes excluded)
+            ms = K * sum(per_ms.values())
 
-        # unfused baseline: same step, one kernel per operator
-        uk = max(3, args.steps // 4)
-        for _ in range(2):
-            step(unfused=True)
+        # unfused baseline: the same step, one kernel per operator
+        uops = [o for o in ops if o.unfused]
+        uk = max(3, min(K, 20))
+        for o in uops:
+            o.unfused()
         torch.cuda.synchronize()
-        u0 = torch.cuda.Event(enable_timing=True)
-        u1 = torch.cuda.Event(enable_timing=True)
-        u0.record(stream)
+        uev = {o.key: [] for o in uops}
         for _ in range(uk):
-            step(unfused=True)
-        u1.record(stream)
+            for o in uops:
+                fl()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                o.unfused()
+                b.record(stream)
+                uev[o.key].append((a, b))
         torch.cuda.synchronize()
-        ums = u0.elapsed_time(u1) / uk
+        u_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in uev.items()}
+        e2e = None
+        if args.workload in ("expr8192", "expr8192_f64"):
+            e2e = e2e_run(fx, torch, stream, sp, keep, storage, K, args.size)
 
-        # end to end through the C ABI with host buffers: inputs copied in,
-        # every output copied back, each step
-        hz = torch.empty(R * C, dtype=tdt).pin_memory()
-        hsmall = {k: torch.empty_like(outs[k], device="cpu").pin_memory()
-                  for k in ("colsum", "rowmax", "nrm")}
-        hin = [host[s].data_ptr() for s in "XYWV"]
-
-        def e2e_step():
-            fx.fx_eval_host(ex["Z"], hin, [hz.data_ptr()], sp)
-            for _, key in TREES[1:]:
-                fx.fx_eval(ex[key], sp)
-                hsmall[key].copy_(outs[key], non_blocking=True)
-
-        ek = max(3, args.steps // 4)
-        e2e_step()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(ek):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1) / ek
-
+    fused_u = sum(per_ms[k] for k in u_ms)
     if world > 1:
-        t = torch.tensor([ms, ums, ems], device=dev)
+        t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ums, ems = (float(x) for x in t.tolist())
+        ms = float(t.item())
     if rank != 0:
         return
-    for h in ex.values():
-        fx.fx_expr_destroy(h)
-    peak, peak_kind = measured_peaks()
-    value = world * step_bytes * args.steps / (ms / 1e3) / 1e9
-    z_gbs = bytes_["Z"] / (z_ms / 1e3) / 1e9
-    khash = kernel_source_hash()
-    tr = TRAFFIC.get(("Z", storage))
-    traffic = tr["bytes"] if tr and tr["hash"] == khash else None
-
+    peak, peak_kind = measured_peak()
+    value = world * step_bytes * K / (ms / 1e3) / 1e9
+    dom_op = next(o for o in ops if o.key == dom)
+    z_gbs = dom_op.bytes / (per_ms[dom] / 1e3) / 1e9
+    tr = TRAFFIC.get((args.workload, dom))
+    traffic = tr["bytes"] if tr and tr["hash"] == kernel_source_hash() else None
     cpu = None
-    if world == 1 and not args.no_cpu:
-        t_cpu, b_cpu = cpu_oracle_time(R, C, args.cpu_cols, storage)
+    if world == 1 and args.workload == "expr8192" and args.size == 8192 and not args.no_cpu:
+        t_cpu, b_cpu = cpu_oracle_time(8192, args.cpu_cols, "f32")
         cpu = {"value": round(b_cpu / t_cpu / 1e9, 4), "unit": "GB/s", "cores": 1,
                "kind": "oracle",
-               "sample": f"{R}x{args.cpu_cols} column panel of each input, all four trees, "
-                         "FP64 numpy tree walker, single thread"}
-    h2d = 4 * R * C * es
-    d2h = R * C * es + (R + C + 1) * es
+               "sample": f"8192x{args.cpu_cols} column panel of X,Y,W,V, all four trees, "
+                         "FP64 numpy tree walker, one thread"}
+    cfg["parallelism"] = f"replicas x{world}"
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms / K, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": storage,
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rows": R, "cols": C, "layout": "column-major",
-                   "inputs": "X,Y,W,V i.i.d. N(0,1), seed 1",
-                   "l2": "inputs larger than L2 (256 MiB each), no flush",
-                   "parallelism": f"replicas x{world}"},
+        "data": "synthetic", "config": cfg,
         "pct_of_peak": round(100 * value / world / peak, 2),
         "pct_of_8tbs_spec": round(100 * value / world / 8000, 2),
-        "vs_unfused": round(ums / (ms / args.steps), 3),
-        "unfused_ms_per_step": round(ums, 4),
-        "per_tree_bytes": bytes_,
+        "vs_unfused": round(sum(u_ms.values()) / fused_u, 3) if u_ms else None,
+        "per_op": {k: {"ms": round(per_ms[k], 4), "bytes": next(o.bytes for o in ops if o.key == k),
+                       "gbs": round(next(o.bytes for o in ops if o.key == k) / per_ms[k] / 1e6, 1),
+                       "unfused_ms": round(u_ms[k], 4) if k in u_ms else None}
+                   for k in per_ms},
         "roofline": {"bound": "hbm", "achieved": round(z_gbs, 2), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(z_gbs / peak, 4),
-                     "traffic": traffic, "kernel": "k_flat (Z tree)",
-                     "alg_bytes_per_launch": bytes_["Z"], "avg_launch_ms": round(z_ms, 4)},
-        "e2e": {"value": round(world * step_bytes / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": round(ems, 3)},
+                     "traffic": traffic, "kernel": dom,
+                     "alg_bytes_per_launch": dom_op.bytes, "avg_launch_ms": round(per_ms[dom], 4)},
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if e2e:
+        line["e2e"] = e2e
     print(json.dumps(line), flush=True)
+
+
+def e2e_run(fx, torch, stream, sp, keep, storage, K, size):
+    """Same step through fx_eval_host: the four inputs copied in from pinned
+    host memory and every output copied back, each step."""
+    env = keep["env"]
+    d = keep["inputs"]
+    host = {k: torch.from_numpy(env[k].data).pin_memory() for k in "XYWV"}
+    hz_t, hz = keep["Z"][1], None
+    hz = torch.empty(hz_t.numel(), dtype=hz_t.dtype).pin_memory()
+    small = {k: (keep[k][1], torch.empty(keep[k][1].numel(), dtype=keep[k][1].dtype).pin_memory())
+             for k in ("colsum", "rowmax", "nrm")}
+    hin = [host[s].data_ptr() for s in "XYWV"]
+
+    def step():
+        fx.fx_eval_host(keep["Z"][0], hin, [hz.data_ptr()], sp)
+        for k, (dev_t, host_t) in small.items():
+            fx.fx_eval(keep[k][0], sp)
+            host_t.copy_(dev_t, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    ek = max(3, min(K, 20))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ek):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1) / ek
+    es = 8 if storage == "f64" else 4
+    R = C = size
+    N = R * C
+    step_bytes = 5 * N * es + (2 * N * es + C * es) + (2 * N * es + R * es) + (2 * N * es + es)
+    return {"value": round(step_bytes / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": 4 * N * es, "d2h_bytes_per_step": N * es + (R + C + 1) * es,
+            "ms_per_step": round(ems, 3),
+            "path": "fx_eval_host (pinned host inputs in, Z out) + 3 fx_eval + small D2H reads"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--workload", default="expr8192",
+                    choices=["expr8192", "expr8192_f64", "small1024", "prec16384_bf16",
+                             "prec16384_f16", "batch4096", "loss8192_f32", "loss8192_bf16"])
+    ap.add_argument("--size", type=int, default=8192, help="rows = cols of the expr8192 trees")
     ap.add_argument("--tune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-cols", type=int, default=4096)
@@ -353,16 +558,16 @@ def main():
         ap.error("--warmup must be at least 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if world > 1 and args.impl == "ours":
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        if args.impl == "reference":
-            run_reference(args, rank, world)
-        else:
-            run_ours(args, rank, world)
+        run_ours(args, rank, world)
     finally:
-        if world > 1 and args.impl == "ours":
+        if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
 

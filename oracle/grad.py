@@ -148,3 +148,113 @@ def gradient_rows(node, env, rows, gL=1.0) -> dict:
     R = np.asarray(rows, dtype=np.int64)[:, None]
     occ = local_adjoints(inner, env, R, np.arange(c)[None, :], gL)
     return _scatter(env, occ)
+
+
+# ---------------------------------------------------------------- error bound of a gradient
+#
+# sigma for the reverse pass, in units of the unit roundoff (first order):
+# the adjoint handed to an operand is c = adj * p, where p is the node's
+# local partial derivative computed from forward values; its bound is
+#     sigma_c = sigma_adj |p| + |adj| sigma_p + |c|
+# with sigma_p the bound of computing p from operands (value, sigma) as
+# given by expr.at_sigma. Contributions summed into one stored element add
+# the rounding of that sum (sum |c|). The root adjoint gL is exact.
+
+def _partials_sigma(op, n, env, R, C):
+    """[(operand node, p, sigma_p), ...] for one operator node."""
+    from .expr import at_sigma, _apply_unary, _EXACT_UNARY
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        if op in UNARY:
+            a, sa = at_sigma(n.args[0], env, R, C)
+            z, sz = at_sigma(n, env, R, C)
+            if op == "neg":
+                return [(n.args[0], -np.ones_like(a), 0.0)]
+            if op == "abs":
+                return [(n.args[0], np.sign(a), 0.0)]
+            if op == "exp":
+                return [(n.args[0], z, sz)]
+            if op == "log":
+                p = 1.0 / a
+                return [(n.args[0], p, sa / (a * a) + np.abs(p))]
+            if op == "sqrt":
+                p = 0.5 / z
+                return [(n.args[0], p, 0.5 * sz / (z * z) + np.abs(p))]
+            if op == "square":
+                return [(n.args[0], 2.0 * a, 2.0 * sa)]
+            if op == "sigmoid":
+                p = z * (1.0 - z)
+                return [(n.args[0], p, np.abs(1.0 - 2.0 * z) * sz + 2.0 * np.abs(p))]
+            if op == "tanh":
+                p = 1.0 - z * z
+                return [(n.args[0], p, 2.0 * np.abs(z) * sz + z * z + np.abs(p))]
+        if op == "pow":
+            a, sa = at_sigma(n.args[0], env, R, C)
+            k = n.args[1].value
+            p = k * np.power(a, k - 1)
+            return [(n.args[0], p, np.abs(k * (k - 1) * np.power(a, k - 2)) * sa + np.abs(p))]
+        if op == "gt":
+            return []
+        x, y = n.args
+        a, sa = at_sigma(x, env, R, C)
+        b, sb = at_sigma(y, env, R, C)
+        if op == "+":
+            return [(x, 1.0, 0.0), (y, 1.0, 0.0)]
+        if op == "-":
+            return [(x, 1.0, 0.0), (y, -1.0, 0.0)]
+        if op in ("%", "*"):
+            return [(x, b, sb), (y, a, sa)]
+        if op == "/":
+            pa = 1.0 / b
+            pb = -a / (b * b)
+            spa = sb / (b * b) + np.abs(pa)
+            spb = sa / (b * b) + 2.0 * np.abs(a) * sb / np.abs(b) ** 3 + 2.0 * np.abs(pb)
+            return [(x, pa, spa), (y, pb, spb)]
+    raise ValueError(op)
+
+
+def _backprop_sigma(n, env, R, C, adj, sadj, out):
+    op = n.op
+    if op == "num":
+        return
+    if op == "leaf":
+        out.append((n.name, R, C, adj, sadj))
+        return
+    if op == "t":
+        _backprop_sigma(n.args[0], env, C, R, adj, sadj, out)
+        return
+    if op == "each_col":
+        _backprop_sigma(n.args[0], env, R, np.zeros_like(np.asarray(C)), adj, sadj, out)
+        return
+    if op == "each_row":
+        _backprop_sigma(n.args[0], env, np.zeros_like(np.asarray(R)), C, adj, sadj, out)
+        return
+    if _is_product(n):
+        raise ValueError("no fused gradient through a matrix product")
+    for child, p, sp in _partials_sigma(op, n, env, R, C):
+        if child.op == "num":
+            continue
+        with np.errstate(over="ignore", invalid="ignore"):
+            c = adj * p
+            sc = sadj * np.abs(p) + np.abs(adj) * sp + np.abs(c)
+        _backprop_sigma(child, env, R, C, c, sc, out)
+
+
+def gradient_sigma(node, env, gL=1.0, rows=None) -> dict:
+    """``{leaf name: (flat indices, gradient values, sigma)}`` of ``gL * accu(f)``
+    over every output element, or over the output rows ``rows`` (see
+    ``gradient_rows`` for when that gives exact entries)."""
+    inner = _check_root(node)
+    r, c = shape_of(inner, env)
+    R = np.arange(r)[:, None] if rows is None else np.asarray(rows, dtype=np.int64)[:, None]
+    Cc = np.arange(c)[None, :]
+    shape = np.broadcast_shapes(R.shape, Cc.shape)
+    occ = []
+    _backprop_sigma(parse(inner), env, R, Cc, np.full(shape, float(gL)), np.zeros(shape), occ)
+    vals = _scatter(env, [(nm, Rl, Cl, a) for nm, Rl, Cl, a, _ in occ])
+    sigs = _scatter(env, [(nm, Rl, Cl, s + np.abs(a)) for nm, Rl, Cl, a, s in occ])
+    out = {}
+    for name, (idx, v) in vals.items():
+        idx2, s = sigs[name]
+        assert np.array_equal(idx, idx2)
+        out[name] = (idx, v, s)
+    return out

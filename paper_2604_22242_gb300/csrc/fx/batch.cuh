@@ -63,12 +63,20 @@ FX_D void batch_tile(const E& e, const Slots& sl, const BatchMat& m, int32_t til
   }
 }
 
+// Matrices whose every full vector is aligned use V-wide tiles, the others
+// scalar tiles; both TR rows high and as wide as two vectors per thread
+// (few registers per thread, so several blocks stay resident per SM).
+template <class E, int V, int TR, int TC, int NT> struct BatchShapes {
+  using Vec = TileShape<E, V, TR, 2 * (NT / (TR / V)), NT>;
+  using One = TileShape<E, 1, TR, 2 * (NT / TR), NT>;
+};
+
 template <class E, class T, int V, int TR, int TC, int NT, int KIND, int NIN>
-__global__ void __launch_bounds__(NT) k_batch(const E e, const BatchMat* __restrict__ mats,
-                                              const BatchItem* __restrict__ items,
-                                              const int64_t nitems, double2* part) {
-  using TSv = TileShape<E, V, TR, TC, NT>;
-  using TS1 = TileShape<E, 1, TR, TC, NT>;
+__global__ void __launch_bounds__(NT, 3) k_batch(const E e, const BatchMat* __restrict__ mats,
+                                                 const BatchItem* __restrict__ items,
+                                                 const int64_t nitems, double2* part) {
+  using TSv = typename BatchShapes<E, V, TR, TC, NT>::Vec;
+  using TS1 = typename BatchShapes<E, V, TR, TC, NT>::One;
   using CT = typename TSv::CT;
   __shared__ CT sm[TSv::SMEM > TS1::SMEM ? TSv::SMEM : TS1::SMEM];
   for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -95,7 +103,7 @@ __global__ void __launch_bounds__(256) k_batch_combine(const BatchMat* __restric
   const int lane = threadIdx.x % 32;
   if (i >= nmat) return;  // whole warps leave together
   const BatchMat& m = mats[i];
-  CompSum<double> a;
+  std::conditional_t<std::is_same<RT, double>::value, CompSum<double>, PlainSum<double>> a;
   a.init();
   for (int64_t k = lane; k < m.ntiles; k += 32) {
     double2 q = __ldcg(part + m.first + k);
@@ -250,7 +258,9 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
         m.rows = R;
         m.cols = C;
         m.vec = vec ? 1 : 0;
-        const int64_t nt = ((R + TR - 1) / TR) * ((C + TCc - 1) / TCc);
+        const int tcm = vec ? BatchShapes<E, V, TR, TCc, NT>::Vec::TC
+                            : BatchShapes<E, V, TR, TCc, NT>::One::TC;
+        const int64_t nt = ((R + TR - 1) / TR) * ((C + tcm - 1) / tcm);
         m.first = int64_t(work.size());
         m.ntiles = int32_t(nt);
         for (int64_t t = 0; t < nt; ++t) work.push_back(BatchItem{int32_t(i), int32_t(t)});

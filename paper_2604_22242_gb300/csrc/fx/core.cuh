@@ -195,6 +195,31 @@ template <class CT>
 using ThreadSum = typename std::conditional<std::is_same<CT, double>::value, PlainSum<CT>,
                                             CompSum<CT>>::type;
 
+// ---------------------------------------------------------------- division
+//
+// n / d for a divisor fixed at launch, by a multiply-high, an add and a
+// shift (Granlund and Montgomery, "Division by Invariant Integers using
+// Multiplication", PLDI 1994, Sec. 4): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(m, n) + n) >> l for
+// every 32-bit n, the add done in 64 bits.
+struct FastDiv {
+  uint32_t d, m, l;
+  static FastDiv make(uint32_t d_) {
+    uint32_t l_ = 0;
+    while ((uint64_t(1) << l_) < d_) ++l_;
+    const uint64_t m_ = (((uint64_t(1) << l_) - d_) << 32) / d_ + 1;
+    return FastDiv{d_, uint32_t(m_), l_};
+  }
+  FX_HD uint32_t div(uint32_t n) const {
+#ifdef __CUDA_ARCH__
+    const uint32_t hi = __umulhi(m, n);
+#else
+    const uint32_t hi = uint32_t((uint64_t(m) * n) >> 32);
+#endif
+    return uint32_t((uint64_t(hi) + n) >> l);
+  }
+};
+
 // NaN-propagating maximum (fmax would drop a NaN operand).
 FX_D float max_nan(float a, float b) { return (a > b || a != a) ? a : b; }
 FX_D double max_nan(double a, double b) { return (a > b || a != a) ? a : b; }

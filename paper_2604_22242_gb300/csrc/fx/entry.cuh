@@ -40,7 +40,7 @@ inline fx_status run_tune(fx_expr* x, int mode, cudaStream_t st, EvalFn ev) {
     return FX_OK;
   }
   static const int blocks[] = {128, 256, 512};
-  static const int unrolls[] = {1, 2, 4};
+  static const int unrolls[] = {2, 4, 8};
   static const int bpss[] = {0, 2, 4};
   cudaEvent_t a, b;
   FX_CUDA(cudaEventCreate(&a));

@@ -92,15 +92,39 @@ FX_D int clamp_valid(int64_t left, int V) {
 
 // ---------------------------------------------------------------- leaf loads
 
-// Flat layout (all leaves MN and contiguous): element i of every leaf.
+// Flat layout: element i = r + c*R of every leaf. Matrix leaves are dense
+// (ld == R) and read at i; an each_col vector at r (i and R are multiples
+// of V, so the V elements share one column); an each_row vector at c.
 template <class LL, int V, class CT, int I = 0>
-FX_D void load_flat(Pack<LL, V, CT>& p, const Slots& sl, int64_t i) {
+FX_D void load_flat(Pack<LL, V, CT>& p, const Slots& sl, int64_t i, int64_t r, int64_t c) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
     using T = typename L::elem;
-    static_assert(L::mode == MN, "flat kernels take plain leaves only");
-    vload(pget<I>::of(p), static_cast<const T*>(sl.s[L::slot].p) + i);
-    load_flat<LL, V, CT, I + 1>(p, sl, i);
+    static_assert(L::mode != MT, "flat kernels take no transposed leaf");
+    auto& dst = pget<I>::of(p);
+    const SlotView& s = sl.s[L::slot];
+    const T* base = static_cast<const T*>(s.p);
+    if constexpr (L::mode == MN) {
+      vload(dst, base + i);
+    } else if constexpr (L::mode == MBC) {
+      if (s.vs == 1) {
+        vload(dst, base + r);
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) dst.v[j] = sload(base + (r + j) * s.vs);
+      }
+    } else {
+      dst.v[0] = sload(base + c * s.vs);
+    }
+    load_flat<LL, V, CT, I + 1>(p, sl, i, r, c);
+  }
+}
+
+template <class LL, int I = 0> FX_HD constexpr int count_bcast() {
+  if constexpr (I < tl_size<LL>::value) {
+    return (tl_at<LL, I>::type::mode >= MBC ? 1 : 0) + count_bcast<LL, I + 1>();
+  } else {
+    return 0;
   }
 }
 
@@ -245,10 +269,14 @@ template <class CT> FX_D CT block_max(CT m) {
   return m;
 }
 
-// Fixed-order FP64 compensated sum of n partial pairs part[i*stride]; the
-// result is valid in thread 0. Every thread of the block must call it.
-FX_D double block_sum_partials(const double2* part, int64_t n, int64_t stride) {
-  CompSum<double> a;
+// Fixed-order FP64 sum of n partial pairs part[i*stride]; the result is
+// valid in thread 0. Every thread of the block must call it. COMP selects
+// a compensated sum (FP64 trees, whose 1e-13 bound needs it); for FP32
+// trees a plain FP64 sum of the partials is already about 2^-40 relative,
+// and FP64 operations are scarce on this part.
+template <bool COMP> FX_D double block_sum_partials(const double2* part, int64_t n, int64_t stride) {
+  using S = std::conditional_t<COMP, CompSum<double>, PlainSum<double>>;
+  S a;
   a.init();
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     double2 q = __ldcg(part + i * stride);
@@ -272,7 +300,7 @@ template <class CT, bool SQRT, class S> FX_D void finish_full_reduce(S& a, const
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double tot = block_sum_partials(red.part, gridDim.x, 1);
+  double tot = block_sum_partials<std::is_same<CT, double>::value>(red.part, gridDim.x, 1);
   if (threadIdx.x == 0) {
     if (SQRT) tot = ::sqrt(tot);
     *static_cast<CT*>(red.out) = static_cast<CT>(tot);
@@ -282,11 +310,14 @@ template <class CT, bool SQRT, class S> FX_D void finish_full_reduce(S& a, const
 
 // ---------------------------------------------------------------- A3: flat stream
 
+// With broadcast leaves, (r, c) of element i comes from one division by R
+// per vector (FastDiv; the host guarantees n < 2^32 and R % V == 0).
 template <class E, class Epi, int V, int U>
 __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const int64_t n,
-                                              const Epi epi, const RedArgs red) {
+                                              const Epi epi, const RedArgs red, const FastDiv fd) {
   using LL = leaves_t<E>;
   using CT = ct_of<E>;
+  constexpr bool BC = count_bcast<LL>() > 0;
   const int64_t nv = n / V;
   const int64_t bdim = blockDim.x;
   const int64_t step = int64_t(gridDim.x) * bdim * U;
@@ -297,7 +328,14 @@ __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const i
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t vi = b + u * bdim;
-      if (vi < nv) load_flat(p[u], sl, vi * V);
+      if (vi < nv) {
+        int64_t r = 0, c = 0;
+        if constexpr (BC) {
+          c = fd.div(uint32_t(vi * V));
+          r = vi * V - c * fd.d;
+        }
+        load_flat(p[u], sl, vi * V, r, c);
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -309,10 +347,10 @@ __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const i
       }
     }
   }
-  if (V > 1 && blockIdx.x == 0) {  // the n % V trailing elements, one lane each
+  if (V > 1 && !BC && blockIdx.x == 0) {  // the n % V trailing elements, one lane each
     for (int64_t i = nv * V + threadIdx.x; i < n; i += bdim) {
       Pack<LL, 1, CT> q;
-      load_flat(q, sl, i);
+      load_flat(q, sl, i, 0, 0);
       CT v1[1];
       eval_lanes<1>(e, q, v1);
       CT v[V];
@@ -622,25 +660,66 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the S partials of each of the thread's rows, in split order; for a
+  // fixed split a warp reads 32*V contiguous values; 8 splits in flight
+  constexpr int KU = 8;
+  if (ISMAX) {
+    const CT* pm = static_cast<const CT*>(rr.partm);
+    CT mm[V];
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
-    if (j < nvalid) {
-      if (ISMAX) {
-        CT mm = neg_inf<CT>();
-        for (int k = 0; k < rr.S; ++k)
-          mm = max_nan(mm, __ldcg(static_cast<const CT*>(rr.partm) + int64_t(k) * R + r + j));
-        out[r + j] = mm;
-      } else {
-        CompSum<double> a;
-        a.init();
-        for (int k = 0; k < rr.S; ++k) {
-          double2 q = __ldcg(rr.part + int64_t(k) * R + r + j);
-          a.add(q.x);
-          a.add(q.y);
-        }
-        out[r + j] = CT(a.s + a.c);
-      }
+    for (int j = 0; j < V; ++j) mm[j] = neg_inf<CT>();
+    int k = 0;
+    for (; k + KU <= rr.S; k += KU) {
+      CT q[KU][V];
+#pragma unroll
+      for (int t = 0; t < KU; ++t)
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          q[t][j] = j < nvalid ? __ldcg(pm + int64_t(k + t) * R + r + j) : neg_inf<CT>();
+#pragma unroll
+      for (int t = 0; t < KU; ++t)
+#pragma unroll
+        for (int j = 0; j < V; ++j) mm[j] = max_nan(mm[j], q[t][j]);
     }
+    for (; k < rr.S; ++k)
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid) mm[j] = max_nan(mm[j], __ldcg(pm + int64_t(k) * R + r + j));
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      if (j < nvalid) out[r + j] = mm[j];
+  } else {
+    using S = std::conditional_t<std::is_same<CT, double>::value, CompSum<double>, PlainSum<double>>;
+    S a[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) a[j].init();
+    int k = 0;
+    for (; k + KU <= rr.S; k += KU) {
+      double2 q[KU][V];
+#pragma unroll
+      for (int t = 0; t < KU; ++t)
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          q[t][j] = j < nvalid ? __ldcg(rr.part + int64_t(k + t) * R + r + j) : make_double2(0, 0);
+#pragma unroll
+      for (int t = 0; t < KU; ++t)
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          a[j].add(q[t][j].x);
+          a[j].add(q[t][j].y);
+        }
+    }
+    for (; k < rr.S; ++k)
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid) {
+          double2 q = __ldcg(rr.part + int64_t(k) * R + r + j);
+          a[j].add(q.x);
+          a[j].add(q.y);
+        }
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      if (j < nvalid) out[r + j] = CT(a[j].s + a[j].c);
   }
   if (threadIdx.x == 0) rr.tickets[blockIdx.x] = 0u;
 }
@@ -728,7 +807,7 @@ FX_D void bwd_bc_finish(const GradArgs& ga, int64_t r, int64_t R, int nvalid) {
 #pragma unroll
         for (int j = 0; j < V; ++j) {
           if (j < nvalid) {
-            CompSum<double> a;
+            std::conditional_t<std::is_same<CT, double>::value, CompSum<double>, PlainSum<double>> a;
             a.init();
             for (int k = 0; k < ga.S; ++k) {
               double2 q = __ldcg(ga.part + (int64_t(b) * ga.S + k) * R + r + j);

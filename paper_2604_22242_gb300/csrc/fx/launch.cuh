@@ -94,25 +94,34 @@ template <class LL, int I = 0> FX_HD constexpr bool all_mn() {
   }
 }
 
-// Flat stream needs every leaf dense (ld == rows) and aligned to A bytes.
-template <class LL, int I = 0> bool leaves_flat(const Binding* b, size_t a) {
-  if constexpr (I < tl_size<LL>::value) {
-    using L = typename tl_at<LL, I>::type;
-    const Binding& x = b[L::slot];
-    if (!(x.ld == x.rows || x.cols <= 1)) return false;
-    if (!aligned(x.p, a)) return false;
-    return leaves_flat<LL, I + 1>(b, a);
-  }
-  return true;
-}
+// Flat stream: every matrix leaf dense (ld == rows); for the vector path
+// also every matrix leaf and unit-stride each_col vector aligned to A bytes.
 template <class LL, int I = 0> bool leaves_dense(const Binding* b) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
     const Binding& x = b[L::slot];
-    if (!(x.ld == x.rows || x.cols <= 1)) return false;
+    if (L::mode == MN && !(x.ld == x.rows || x.cols <= 1)) return false;
     return leaves_dense<LL, I + 1>(b);
   }
   return true;
+}
+template <class LL, int I = 0> bool leaves_flat(const Binding* b, size_t a) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    const Binding& x = b[L::slot];
+    if (L::mode == MN && !aligned(x.p, a)) return false;
+    if (L::mode == MBC && !(x.rows == 1 && x.cols != 1) && !aligned(x.p, a)) return false;
+    return leaves_flat<LL, I + 1>(b, a);
+  }
+  return true;
+}
+
+// Can the flat stream kernel run this tree at R x C? (no transposed leaf,
+// dense matrix leaves; with broadcast leaves n < 2^32 and R % V == 0)
+template <class LL> bool flat_ok(const Binding* b, int64_t R, int64_t C, int V) {
+  if (count_mt<LL>() > 0 || !leaves_dense<LL>(b)) return false;
+  if (count_bcast<LL>() == 0) return true;
+  return R > 0 && R * C < (int64_t(1) << 32) && R % V == 0;
 }
 
 // Column-vector path: every full V-vector of every matrix leaf is aligned.
@@ -166,24 +175,29 @@ inline fx_status red_space(const Run& r, int grid, RedArgs& red) {
 
 template <class E, class Epi, int V, int U>
 fx_status launch_flat_u(const Run& r, const E& e, const Slots& sl, int64_t n, const Epi& epi,
-                        RedArgs red) {
+                        RedArgs red, int64_t flat_rows) {
   auto kern = k_flat<E, Epi, V, U>;
   const int block = (r.tune.block >= 64 && r.tune.block <= 512) ? r.tune.block : 256;
   const int64_t nv = n / V;
   int64_t work = (nv + int64_t(block) * U - 1) / (int64_t(block) * U);
   const int grid = grid_for(kern, block, work > 0 ? work : 1, r.tune);
   if constexpr (Epi::reduces) FX_TRY(red_space(r, grid, red));
-  kern<<<grid, block, 0, r.st>>>(e, sl, n, epi, red);
+  FastDiv fd{};
+  if constexpr (count_bcast<leaves_t<E>>() > 0) fd = FastDiv::make(uint32_t(flat_rows));
+  kern<<<grid, block, 0, r.st>>>(e, sl, n, epi, red, fd);
   return after_launch(r, "k_flat");
 }
 
 template <class E, class Epi, int V>
 fx_status launch_flat(const Run& r, const E& e, const Slots& sl, int64_t n, const Epi& epi,
-                      RedArgs red) {
+                      RedArgs red, int64_t flat_rows) {
   switch (r.tune.unroll) {
-    case 1: return launch_flat_u<E, Epi, V, 1>(r, e, sl, n, epi, red);
-    case 2: return launch_flat_u<E, Epi, V, 2>(r, e, sl, n, epi, red);
-    default: return launch_flat_u<E, Epi, V, 4>(r, e, sl, n, epi, red);
+    case 2: return launch_flat_u<E, Epi, V, 2>(r, e, sl, n, epi, red, flat_rows);
+    case 8: {  // 8 vectors per leaf in flight only for trees of at most two leaves
+      constexpr int U8 = tl_size<leaves_t<E>>::value <= 2 ? 8 : 4;
+      return launch_flat_u<E, Epi, V, U8>(r, e, sl, n, epi, red, flat_rows);
+    }
+    default: return launch_flat_u<E, Epi, V, 4>(r, e, sl, n, epi, red, flat_rows);
   }
 }
 
@@ -221,11 +235,12 @@ template <class T, class E> fx_status run_elementwise(const Run& r, const E& e) 
   const Slots sl = make_slots(r.b, r.n_in);
   T* z = static_cast<T*>(zb.p);
   const bool zdense = zb.ld == R || C == 1;
-  if constexpr (all_mn<LL>()) {
-    if (zdense && leaves_dense<LL>(r.b)) {
-      if (leaves_flat<LL>(r.b, V * sizeof(T)) && aligned(z, V * sizeof(T)))
-        return launch_flat<E, EpiStore<T, V>, V>(r, e, sl, R * C, EpiStore<T, V>{z, R}, {});
-      return launch_flat<E, EpiStore<T, 1>, 1>(r, e, sl, R * C, EpiStore<T, 1>{z, R}, {});
+  if constexpr (count_mt<LL>() == 0) {
+    if (zdense && flat_ok<LL>(r.b, R, C, 1)) {
+      if (flat_ok<LL>(r.b, R, C, V) && leaves_flat<LL>(r.b, V * sizeof(T)) &&
+          aligned(z, V * sizeof(T)))
+        return launch_flat<E, EpiStore<T, V>, V>(r, e, sl, R * C, EpiStore<T, V>{z, R}, {}, R);
+      return launch_flat<E, EpiStore<T, 1>, 1>(r, e, sl, R * C, EpiStore<T, 1>{z, R}, {}, R);
     }
   }
   if (leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0)
@@ -247,11 +262,14 @@ template <class T, class E> fx_status run_multi(const Run& r, const E& e) {
   RedArgs red{};
   red.out = sb.p;
   const bool zdense = zb.ld == R || C == 1;
-  if constexpr (all_mn<LL>()) {
-    if (zdense && leaves_dense<LL>(r.b)) {
-      if (leaves_flat<LL>(r.b, V * sizeof(T)) && aligned(z, V * sizeof(T)))
-        return launch_flat<E, EpiStoreSum<T, V>, V>(r, e, sl, R * C, EpiStoreSum<T, V>{z, R}, red);
-      return launch_flat<E, EpiStoreSum<T, 1>, 1>(r, e, sl, R * C, EpiStoreSum<T, 1>{z, R}, red);
+  if constexpr (count_mt<LL>() == 0) {
+    if (zdense && flat_ok<LL>(r.b, R, C, 1)) {
+      if (flat_ok<LL>(r.b, R, C, V) && leaves_flat<LL>(r.b, V * sizeof(T)) &&
+          aligned(z, V * sizeof(T)))
+        return launch_flat<E, EpiStoreSum<T, V>, V>(r, e, sl, R * C, EpiStoreSum<T, V>{z, R}, red,
+                                                    R);
+      return launch_flat<E, EpiStoreSum<T, 1>, 1>(r, e, sl, R * C, EpiStoreSum<T, 1>{z, R}, red,
+                                                  R);
     }
   }
   if (leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0)
@@ -276,11 +294,11 @@ template <class T, class Root> fx_status run_full_reduce(const Run& r, const Roo
   const Slots sl = make_slots(r.b, r.n_in);
   RedArgs red{};
   red.out = ob.p;
-  if constexpr (all_mn<LL>()) {
-    if (leaves_dense<LL>(r.b)) {
-      if (leaves_flat<LL>(r.b, V * sizeof(T)))
-        return launch_flat<E, EpiSum<CT, V, SQ>, V>(r, e, sl, R * C, EpiSum<CT, V, SQ>{R}, red);
-      return launch_flat<E, EpiSum<CT, 1, SQ>, 1>(r, e, sl, R * C, EpiSum<CT, 1, SQ>{R}, red);
+  if constexpr (count_mt<LL>() == 0) {
+    if (flat_ok<LL>(r.b, R, C, 1)) {
+      if (flat_ok<LL>(r.b, R, C, V) && leaves_flat<LL>(r.b, V * sizeof(T)))
+        return launch_flat<E, EpiSum<CT, V, SQ>, V>(r, e, sl, R * C, EpiSum<CT, V, SQ>{R}, red, R);
+      return launch_flat<E, EpiSum<CT, 1, SQ>, 1>(r, e, sl, R * C, EpiSum<CT, 1, SQ>{R}, red, R);
     }
   }
   if (leaves_vec<LL, V>(r.b))
@@ -392,7 +410,9 @@ fx_status run_backward(fx_expr* x, const Root& root, const void* gout, void* con
   } else {
     using E = typename root_of<Root>::inner;
     using LL = leaves_t<E>;
-    constexpr int V = vec_width<E, 16>();
+    // 8-byte accesses: the reverse pass keeps one adjoint per leaf per lane
+    // live, so narrower lanes leave room for more resident threads
+    constexpr int V = vec_width<E, 8>() > 0 ? vec_width<E, 8>() : 1;
     constexpr int NT = 256, U = 2;
     constexpr int NBC = count_mode<LL>(MBC);
     const Run r = run_of(x, st);

@@ -68,7 +68,7 @@ fx_status launch_into_scratch(K kern, int block, int64_t work, const E& e, const
   if constexpr (TILED) {
     kern<<<grid, block, 0, st>>>(e, sl, a0, a1, epi, red);
   } else {
-    kern<<<grid, block, 0, st>>>(e, sl, a0, epi, red);
+    kern<<<grid, block, 0, st>>>(e, sl, a0, epi, red, fx::FastDiv{});
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return fx::cuda_fail(err, "no-alloc reduction launch");

@@ -1,0 +1,112 @@
+"""Batched evaluation of Z = A % B + 0.5 * trans(C) and s = accu(Z) over
+many matrices of uneven shapes in one persistent launch (GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from harness import from_device, scaled_error
+
+pytestmark = pytest.mark.gpu
+
+TREE = "(+ (% A B) (* 0.5 (t C)))"
+
+
+@pytest.fixture(scope="module")
+def fx(fxlib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return fxlib
+
+
+def arena(mats, dtype, align=4):
+    """One device buffer holding every matrix, each starting `align` elements aligned."""
+    import torch
+    offs, pos = [], 0
+    for m in mats:
+        offs.append(pos)
+        pos += (m.data.size + align - 1) // align * align
+    host = np.zeros(max(pos, 1), dtype=mats[0].data.dtype if mats else np.float32)
+    for m, o in zip(mats, offs):
+        host[o:o + m.data.size] = m.data
+    return torch.from_numpy(host).cuda(), offs
+
+
+def run_batch(fx, rows, cols, ops, use_graph, repeat=1, storage=0):
+    import torch
+    n = len(rows)
+    A, oa = arena(ops["A"], None)
+    B, ob = arena(ops["B"], None)
+    C, oc = arena(ops["C"], None)
+    zsizes = [synth.Buffer(np.zeros(r * c, np.float32), r, c, max(r, 1), "f32")
+              for r, c in zip(rows, cols)]
+    Z, oz = arena(zsizes, None)
+    Z.fill_(float("nan"))
+    S = torch.full((n,), float("nan"), device="cuda")
+    items = (fx.BatchItem * n)()
+    es = A.element_size()
+    for i in range(n):
+        it = items[i]
+        it.ptr[0] = A.data_ptr() + oa[i] * es
+        it.ptr[1] = B.data_ptr() + ob[i] * es
+        it.ptr[2] = C.data_ptr() + oc[i] * es
+        it.ptr[3] = Z.data_ptr() + oz[i] * es
+        it.ptr[4] = S.data_ptr() + i * 4
+        it.rows, it.cols = int(rows[i]), int(cols[i])
+    h = fx.fx_expr_create("schur_trans_accu", storage)
+    stream = torch.cuda.Stream()
+    try:
+        for _ in range(repeat):
+            fx.fx_eval_batch(h, items, int(stream.cuda_stream), use_graph)
+        stream.synchronize()
+        launches = fx.fx_expr_last_launches(h)
+    finally:
+        fx.fx_expr_destroy(h)
+    zs = []
+    Zh = Z.cpu().numpy()
+    for i in range(n):
+        r, c = int(rows[i]), int(cols[i])
+        zs.append(Zh[oz[i]:oz[i] + r * c].reshape(c, r).T.astype(np.float64) if r * c else
+                  np.zeros((r, c)))
+    return zs, S.cpu().numpy().astype(np.float64), launches
+
+
+def check(ops, rows, cols, zs, ss, which):
+    for i in which:
+        env = {k: ops[k][i] for k in "ABC"}
+        z, sz = oracle.evaluate_sigma(TREE, env)
+        err, _, bad, _ = scaled_error(zs[i], z, sz, "f32")
+        assert bad == 0 and err <= 2e-6, (i, rows[i], cols[i], err)
+        v, sv = oracle.evaluate_sigma(f"(accu {TREE})", env)
+        err, _, bad, _ = scaled_error([ss[i]], [v[0, 0]], [sv[0, 0]], "f32")
+        assert bad == 0 and err <= 1e-5, (i, "s", err)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_small_uneven_batch(fx, use_graph):
+    rows, cols, ops = synth.batch_operands(5, 60, [("A", False), ("B", False), ("C", True)],
+                                           lo=1, hi=300)
+    zs, ss, launches = run_batch(fx, rows, cols, ops, use_graph, repeat=2)
+    check(ops, rows, cols, zs, ss, range(len(rows)))
+    assert launches == 2
+
+
+def test_graph_replay_matches_direct(fx):
+    rows, cols, ops = synth.batch_operands(6, 40, [("A", False), ("B", False), ("C", True)],
+                                           lo=8, hi=200)
+    z1, s1, _ = run_batch(fx, rows, cols, ops, False)
+    z2, s2, _ = run_batch(fx, rows, cols, ops, True, repeat=3)
+    assert np.array_equal(s1, s2)
+    for a, b in zip(z1, z2):
+        assert np.array_equal(a, b)
+
+
+def test_batch_4096_log_uniform(fx):
+    rows, cols, ops = synth.batch_operands(2, 4096, [("A", False), ("B", False), ("C", True)])
+    zs, ss, _ = run_batch(fx, rows, cols, ops, True, repeat=2)
+    rng = np.random.default_rng(2)
+    which = sorted(set(rng.choice(4096, 48, replace=False).tolist()) |
+                   {int(np.argmax(rows * cols)), int(np.argmin(rows * cols))})
+    check(ops, rows, cols, zs, ss, which)
+    assert np.all(np.isfinite(ss))

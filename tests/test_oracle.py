@@ -487,3 +487,26 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.undo()
     assert not np.allclose(bad, oracle.gradient(LOSS, env)["X"])
     assert real_bp is ograd._backprop and np.array_equal(good, oracle.gradient(LOSS, env)["Y"])
+
+
+def test_gradient_sigma_bounds_float32_reverse_pass():
+    """The reverse-pass error bound holds for a step-by-step FP32 evaluation
+    of the loss gradient (closed form of the same reverse pass)."""
+    from oracle import grad as ograd
+    r, c = 40, 30
+    env = synth.operands(3, [("X", r, c), ("W", r, c), ("Y", r, c), ("b", r, 1)], "f32",
+                         "normal_half")
+    f = np.float32
+    X, W, Y = (env[k].data.reshape(c, r).T for k in "XWY")
+    b = env["b"].data[:, None]
+    U = X * W + b
+    S = f(1) / (f(1) + np.exp(-U))
+    G = (f(2) * (S - Y)) * (S * (f(1) - S))
+    g32 = {"X": G * W, "W": G * X, "Y": f(-2) * (S - Y), "b": G.sum(axis=1, dtype=np.float32)[:, None]}
+    gs = ograd.gradient_sigma(LOSS, env)
+    u = 2.0 ** -24
+    for name in "XWYb":
+        idx, v, s = gs[name]
+        got = g32[name].T.ravel().astype(np.float64) if name != "b" else g32[name].ravel()
+        assert np.all(np.abs(got - v) <= 8 * u * s + 1e-300), name
+        assert np.median(s / np.maximum(np.abs(v), 1e-300)) < 100, name
