@@ -188,6 +188,13 @@ fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* b
  * enqueued (for launch accounting). */
 int fx_expr_last_launches(const fx_expr* x);
 
+/* Synchronises `stream`, then reports FX_E_CUDA if an asynchronous CUDA
+ * error is pending or if a kernel of this object gave up one of its bounded
+ * waits (the bulk-copy pipelines poll their shared-memory barriers a fixed
+ * number of times, then record the failure and finish without combining);
+ * the record is cleared. FX_OK otherwise. */
+fx_status fx_expr_sync_status(fx_expr* x, void* stream);
+
 /* ---- evaluation without device allocation ------------------------------ */
 
 /* Bytes of the fixed device array behind fx_sqdiff_accu_f32_noalloc: room

@@ -19,7 +19,7 @@ __all__ = [
     "fx_list", "fx_expr_create", "fx_expr_destroy", "fx_expr_info", "fx_expr_slot_name",
     "fx_expr_bind", "fx_expr_set_scalar", "fx_expr_get_scalar", "fx_eval", "fx_eval_unfused",
     "fx_eval_host", "fx_eval_batch", "fx_eval_backward", "fx_tune", "fx_expr_launch_shape",
-    "fx_expr_last_launches", "fx_last_error_string", "fx_status_string", "BatchItem",
+    "fx_expr_last_launches", "fx_expr_sync_status", "fx_last_error_string", "fx_status_string", "BatchItem",
     "colmajor", "bind_tensor", "Expr", "FusedLoss", "DTYPE_OF",
 ]
 
@@ -79,6 +79,7 @@ def lib():
         "fx_expr_launch_shape": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                       ctypes.POINTER(i32)]),
         "fx_expr_last_launches": (i32, [vp]),
+        "fx_expr_sync_status": (st, [vp, vp]),
         "fx_last_error_string": (ctypes.c_char_p, []),
         "fx_status_string": (ctypes.c_char_p, [i32]),
     }
@@ -186,6 +187,10 @@ def fx_expr_launch_shape(h):
 
 def fx_expr_last_launches(h) -> int:
     return lib().fx_expr_last_launches(h)
+
+
+def fx_expr_sync_status(h, stream: int = 0):
+    _check(lib().fx_expr_sync_status(h, stream or None))
 
 
 def fx_last_error_string() -> str:

@@ -222,6 +222,10 @@ template <class T, int V> struct EpiStoreSum {
 
 // ---------------------------------------------------------------- combines
 
+// Barrier over the first `n` threads of the block (n a multiple of 32):
+// a named barrier, so blocks whose producer warp has left can still sync.
+FX_D void block_sync(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+
 template <class S> FX_D void warp_merge(S& a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -603,42 +607,13 @@ struct RowRed {
   int S;
 };
 
-template <class E, bool ISMAX, int V, int U, int NT>
-__global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int64_t R,
-                                            const int64_t C, const RowRed rr) {
-  using LL = leaves_t<E>;
-  using CT = ct_of<E>;
-  const int64_t r = (int64_t(blockIdx.x) * NT + threadIdx.x) * V;
-  const int nvalid = clamp_valid(R - r, V);
-  const int s = blockIdx.y;
-  const int64_t cb = C * s / rr.S, ce = C * (s + 1) / rr.S;
-  ThreadSum<CT> acc[V];
-  CT m[V];
-#pragma unroll
-  for (int j = 0; j < V; ++j) {
-    acc[j].init();
-    m[j] = neg_inf<CT>();
-  }
-  if (nvalid > 0) {
-    for (int64_t c = cb; c < ce; c += U) {
-      Pack<LL, V, CT> p[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (c + u < ce) load_rc(p[u], sl, r, c + u, nvalid);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (c + u < ce) {
-          CT v[V];
-          eval_lanes<V>(e, p[u], v);
-#pragma unroll
-          for (int j = 0; j < V; ++j) {
-            if (ISMAX) m[j] = max_nan(m[j], v[j]);
-            else acc[j].add(v[j]);
-          }
-        }
-      }
-    }
-  }
+// End of a row-range block: write the thread's rows (one split), or
+// publish per-row partials and let the last of the S splits of this row
+// range (an atomic ticket) combine them in split order. Called by the
+// `nthreads` computing threads only (a named barrier, not __syncthreads).
+template <bool ISMAX, int V, class CT>
+FX_D void row_finish(const RowRed& rr, ThreadSum<CT> (&acc)[V], CT (&m)[V], int64_t R, int64_t r,
+                     int nvalid, int s, int nthreads, const volatile int* abort = nullptr) {
   CT* out = static_cast<CT*>(rr.out);
   if (rr.S == 1) {
 #pragma unroll
@@ -654,10 +629,11 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
     }
   }
   __threadfence();
-  __syncthreads();
+  block_sync(nthreads);
+  if (abort && *abort) return;  // a bounded wait gave up (recorded); no combine
   __shared__ bool last;
   if (threadIdx.x == 0) last = atomicAdd(rr.tickets + blockIdx.x, 1u) == unsigned(rr.S - 1);
-  __syncthreads();
+  block_sync(nthreads);
   if (!last) return;
   __threadfence();
   // the S partials of each of the thread's rows, in split order; for a
@@ -722,6 +698,45 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
       if (j < nvalid) out[r + j] = CT(a[j].s + a[j].c);
   }
   if (threadIdx.x == 0) rr.tickets[blockIdx.x] = 0u;
+}
+
+template <class E, bool ISMAX, int V, int U, int NT>
+__global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int64_t R,
+                                            const int64_t C, const RowRed rr) {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  const int64_t r = (int64_t(blockIdx.x) * NT + threadIdx.x) * V;
+  const int nvalid = clamp_valid(R - r, V);
+  const int s = blockIdx.y;
+  const int64_t cb = C * s / rr.S, ce = C * (s + 1) / rr.S;
+  ThreadSum<CT> acc[V];
+  CT m[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    acc[j].init();
+    m[j] = neg_inf<CT>();
+  }
+  if (nvalid > 0) {
+    for (int64_t c = cb; c < ce; c += U) {
+      Pack<LL, V, CT> p[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c + u < ce) load_rc(p[u], sl, r, c + u, nvalid);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c + u < ce) {
+          CT v[V];
+          eval_lanes<V>(e, p[u], v);
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            if (ISMAX) m[j] = max_nan(m[j], v[j]);
+            else acc[j].add(v[j]);
+          }
+        }
+      }
+    }
+  }
+  row_finish<ISMAX, V, CT>(rr, acc, m, R, r, nvalid, s, NT);
 }
 
 // ---------------------------------------------------------------- A9: fused backward
@@ -823,6 +838,33 @@ FX_D void bwd_bc_finish(const GradArgs& ga, int64_t r, int64_t R, int nvalid) {
   }
 }
 
+// End of a backward row-range block: publish the each_col leaves' row
+// partials; the last of the S splits of the row range combines them.
+// Called by the `nthreads` computing threads only.
+template <class LL, int V, class CT, int NBC, int NB>
+FX_D void bwd_finish(const GradArgs& ga, ThreadSum<CT> (&bacc)[NB][V], int64_t R, int64_t r,
+                     int nvalid, int s, int nthreads, const volatile int* abort = nullptr) {
+  if constexpr (NBC > 0) {
+#pragma unroll
+    for (int b = 0; b < NBC; ++b)
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid)
+          ga.part[(int64_t(b) * ga.S + s) * R + r + j] =
+              make_double2(double(bacc[b][j].s), double(bacc[b][j].c));
+    __threadfence();
+    block_sync(nthreads);
+    if (abort && *abort) return;  // a bounded wait gave up (recorded); no combine
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(ga.tickets + blockIdx.x, 1u) == unsigned(ga.S - 1);
+    block_sync(nthreads);
+    if (!last) return;
+    __threadfence();
+    bwd_bc_finish<LL, V, CT>(ga, r, R, nvalid);
+    if (threadIdx.x == 0) ga.tickets[blockIdx.x] = 0u;
+  }
+}
+
 template <class E, int V, int U, int NT>
 __global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int64_t R,
                                             const int64_t C, const GradArgs ga) {
@@ -864,24 +906,7 @@ __global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int
       }
     }
   }
-  if constexpr (NBC > 0) {
-#pragma unroll
-    for (int b = 0; b < NBC; ++b)
-#pragma unroll
-      for (int j = 0; j < V; ++j)
-        if (j < nvalid)
-          ga.part[(int64_t(b) * ga.S + s) * R + r + j] =
-              make_double2(double(bacc[b][j].s), double(bacc[b][j].c));
-    __threadfence();
-    __syncthreads();
-    __shared__ bool last;
-    if (threadIdx.x == 0) last = atomicAdd(ga.tickets + blockIdx.x, 1u) == unsigned(ga.S - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    bwd_bc_finish<LL, V, CT>(ga, r, R, nvalid);
-    if (threadIdx.x == 0) ga.tickets[blockIdx.x] = 0u;
-  }
+  bwd_finish<LL, V, CT, NBC>(ga, bacc, R, r, nvalid, s, NT);
 }
 
 }  // namespace fx

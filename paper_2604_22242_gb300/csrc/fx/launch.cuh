@@ -6,10 +6,12 @@
 #include <cmath>
 #include <string>
 
-#include "kernels.cuh"
+#include "bulk.cuh"
 #include "runtime.hpp"
 
 namespace fx {
+
+inline bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
 // What one evaluation sees: bindings (inputs, then outputs), launch shape,
 // the reduction workspace and a launch counter.
@@ -20,13 +22,59 @@ struct Run {
   Workspace* ws;
   int* launches;
   cudaStream_t st;
+  Workspace* errws;  // error word of the bulk kernels' bounded waits
 };
 
 inline Run run_of(fx_expr* x, cudaStream_t st) {
-  return Run{x->b, x->e->n_in, x->tune, &x->ws, &x->last_launches, st};
+  return Run{x->b, x->e->n_in, x->tune, &x->ws, &x->last_launches, st, &x->ws_err};
 }
 
-inline bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
+inline fx_status err_word(const Run& r, unsigned int** out) {
+  FX_TRY(r.errws->ensure(256, r.st));
+  *out = static_cast<unsigned int*>(r.errws->p);
+  return FX_OK;
+}
+
+// Bulk copies need every plain leaf 16-byte aligned with 16-byte column
+// strides, and whole rows of the last row range in multiples of 16 bytes.
+template <class LL, int I = 0> bool leaves_bulk(const Binding* b, int64_t R) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    const size_t es = sizeof(typename L::elem);
+    if constexpr (L::mode == MN) {
+      const Binding& x = b[L::slot];
+      if (!aligned(x.p, 16) || (size_t(x.ld) * es) % 16 != 0 || (size_t(R) * es) % 16 != 0)
+        return false;
+    } else if constexpr (L::mode == MT) {
+      return false;
+    }
+    return leaves_bulk<LL, I + 1>(b, R);
+  }
+  return true;
+}
+
+// Dynamic shared memory above 48 KB must be allowed once per kernel.
+template <class K> fx_status allow_smem(K kern, int bytes) {
+  static bool done = false;  // one flag per kernel instantiation
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
+    done = true;
+  }
+  return FX_OK;
+}
+
+// Column splits for row-range kernels: enough blocks for the resident
+// capacity, at least 2*minc columns per split.
+inline int64_t row_splits(int64_t gx, int64_t C, int occ, int minc, const Tune& t) {
+  const int sms = device_sms() > 0 ? device_sms() : 1;
+  const int bps = t.bps > 0 ? (t.bps < occ ? t.bps : occ) : occ;
+  int64_t S = (int64_t(sms) * (bps > 0 ? bps : 1) + gx - 1) / gx;
+  const int64_t smax = C / (2 * minc) > 1 ? C / (2 * minc) : 1;
+  if (S > smax) S = smax;
+  if (S > 65535) S = 65535;
+  return S < 1 ? 1 : S;
+}
 
 inline Slots make_slots(const Binding* b, int n) {
   Slots s{};
@@ -315,7 +363,7 @@ template <class E, int D> struct dim_of<MaxDim<E, D>> { static constexpr int d =
 template <class E, bool ISMAX, int V>
 fx_status launch_col(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C, void* out,
                      int64_t ldo) {
-  constexpr int NT = 256, U = 4;
+  constexpr int NT = 256, U = tl_size<leaves_t<E>>::value <= 2 ? 8 : 4;
   if (R >= 1024) {
     auto kern = k_col<E, ISMAX, V, U, NT, NT>;
     const int grid = grid_for(kern, NT, C > 0 ? C : 1, r.tune);
@@ -332,32 +380,48 @@ fx_status launch_col(const Run& r, const E& e, const Slots& sl, int64_t R, int64
 template <class E, bool ISMAX, int V>
 fx_status launch_row(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C, void* out) {
   using CT = ct_of<E>;
-  constexpr int NT = 256, U = 4;
-  auto kern = k_row<E, ISMAX, V, U, NT>;
-  const int64_t gx = (R + int64_t(NT) * V - 1) / (int64_t(NT) * V);
-  const int sms = device_sms() > 0 ? device_sms() : 1;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1) occ = 1;
-  const int bps = r.tune.bps > 0 ? (r.tune.bps < occ ? r.tune.bps : occ) : occ;
-  const int64_t target = int64_t(sms) * bps;
-  int64_t S = (target + gx - 1) / gx;
-  const int64_t smax = C / (2 * U) > 1 ? C / (2 * U) : 1;
-  if (S > smax) S = smax;
-  if (S > 65535) S = 65535;
-  if (S < 1) S = 1;
+  using LL = leaves_t<E>;
+  // ~128 KB in flight per SM: 8 column vectors per thread for 1-2 leaves
+  constexpr int NT = 256, U = tl_size<LL>::value <= 2 ? 8 : 4, NS = 4;
   RowRed rr{};
   rr.out = out;
-  rr.S = int(S);
-  if (S > 1) {
-    const size_t part = size_t(S) * R * sizeof(double2);
-    const size_t partm = size_t(S) * R * sizeof(CT);
-    const size_t tick = size_t(gx) * sizeof(unsigned int);
-    FX_TRY(r.ws->ensure(part + partm + tick + 512, r.st));
-    char* w = static_cast<char*>(r.ws->p);
-    rr.part = reinterpret_cast<double2*>(w);
-    rr.partm = w + part;
-    rr.tickets = reinterpret_cast<unsigned int*>(w + ((part + partm + 255) & ~size_t(255)));
+  auto space = [&](int64_t gx, int64_t S) -> fx_status {
+    rr.S = int(S);
+    if (S > 1) {
+      const size_t part = size_t(S) * R * sizeof(double2);
+      const size_t partm = size_t(S) * R * sizeof(CT);
+      const size_t tick = size_t(gx) * sizeof(unsigned int);
+      FX_TRY(r.ws->ensure(part + partm + tick + 512, r.st));
+      char* w = static_cast<char*>(r.ws->p);
+      rr.part = reinterpret_cast<double2*>(w);
+      rr.partm = w + part;
+      rr.tickets = reinterpret_cast<unsigned int*>(w + ((part + partm + 255) & ~size_t(255)));
+    }
+    return FX_OK;
+  };
+  if constexpr (V > 1) {
+   if (r.tune.bulk && leaves_bulk<LL>(r.b, R)) {
+    constexpr int CPS = 2;
+    auto kern = k_row_bulk<E, ISMAX, V, NT, NS, CPS>;
+    constexpr int smem = NS * CPS * stage_bytes<LL, NT * V>() + int(sizeof(Ring<NS>));
+    FX_TRY(allow_smem(kern, smem));
+    unsigned int* err = nullptr;
+    FX_TRY(err_word(r, &err));
+    const int64_t gx = (R + int64_t(NT) * V - 1) / (int64_t(NT) * V);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem) != cudaSuccess || occ < 1) occ = 1;
+    const int64_t S = row_splits(gx, C, occ, 2 * NS * CPS, r.tune);
+    FX_TRY(space(gx, S));
+    kern<<<dim3(unsigned(gx), unsigned(S)), NT + 32, smem, r.st>>>(e, sl, R, C, rr, err);
+    return after_launch(r, "k_row_bulk");
   }
+  }
+  auto kern = k_row<E, ISMAX, V, U, NT>;
+  const int64_t gx = (R + int64_t(NT) * V - 1) / (int64_t(NT) * V);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1) occ = 1;
+  const int64_t S = row_splits(gx, C, occ, U, r.tune);
+  FX_TRY(space(gx, S));
   kern<<<dim3(unsigned(gx > 0 ? gx : 1), unsigned(S)), NT, 0, r.st>>>(e, sl, R, C, rr);
   return after_launch(r, "k_row");
 }
@@ -435,16 +499,7 @@ fx_status run_backward(fx_expr* x, const Root& root, const void* gout, void* con
       return FX_OK;
     }
     const Slots sl = make_slots(r.b, r.n_in);
-    auto go = [&](auto kern, int v) -> fx_status {
-      const int64_t gx = (R + int64_t(NT) * v - 1) / (int64_t(NT) * v);
-      const int sms = device_sms() > 0 ? device_sms() : 1;
-      int occ = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1) occ = 1;
-      int64_t S = (int64_t(sms) * occ + gx - 1) / gx;
-      const int64_t smax = C / (2 * U) > 1 ? C / (2 * U) : 1;
-      if (S > smax) S = smax;
-      if (S > 65535) S = 65535;
-      if (S < 1) S = 1;
+    auto space = [&](int64_t gx, int64_t S) -> fx_status {
       ga.S = int(S);
       if (NBC > 0) {
         const size_t part = size_t(NBC) * S * R * sizeof(double2);
@@ -452,6 +507,36 @@ fx_status run_backward(fx_expr* x, const Root& root, const void* gout, void* con
         ga.part = static_cast<double2*>(x->ws.p);
         ga.tickets = reinterpret_cast<unsigned int*>(static_cast<char*>(x->ws.p) + ((part + 255) & ~size_t(255)));
       }
+      return FX_OK;
+    };
+    // bulk-copy pipeline when every plain leaf and gradient allows 16-byte copies
+    // thread lanes of 8 bytes (2 FP32, 4 BF16/FP16, 1 FP64): the reverse pass
+    // keeps one adjoint per leaf per lane live
+    constexpr int VB = vec_width<E, 8>();
+    bool bulk = VB > 1 && leaves_bulk<LL>(r.b, R) && R % VB == 0;
+    for (int k = 0; k < r.n_in; ++k)
+      if (grads[k] && !aligned(grads[k], 16)) bulk = false;
+    if (bulk) {
+      constexpr int NS = 4, CPS = 4;
+      auto kern = k_bwd_bulk<E, VB, NT, NS, CPS>;
+      constexpr int smem = NS * CPS * stage_bytes<LL, NT * VB>() + int(sizeof(Ring<NS>));
+      FX_TRY(allow_smem(kern, smem));
+      unsigned int* err = nullptr;
+      FX_TRY(err_word(r, &err));
+      const int64_t gx = (R + int64_t(NT) * VB - 1) / (int64_t(NT) * VB);
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem) != cudaSuccess || occ < 1) occ = 1;
+      const int64_t S = row_splits(gx, C, occ, 2 * NS * CPS, r.tune);
+      FX_TRY(space(gx, S));
+      kern<<<dim3(unsigned(gx), unsigned(S)), NT + 32, smem, st>>>(e, sl, R, C, ga, err);
+      return after_launch(r, "k_bwd_bulk");
+    }
+    auto go = [&](auto kern, int v) -> fx_status {
+      const int64_t gx = (R + int64_t(NT) * v - 1) / (int64_t(NT) * v);
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1) occ = 1;
+      const int64_t S = row_splits(gx, C, occ, U, r.tune);
+      FX_TRY(space(gx, S));
       kern<<<dim3(unsigned(gx), unsigned(S)), NT, 0, st>>>(e, sl, R, C, ga);
       return after_launch(r, "k_bwd");
     };

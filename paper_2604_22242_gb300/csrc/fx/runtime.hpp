@@ -26,6 +26,7 @@ struct Tune {
   int unroll = 4;
   int bps = 0;
   bool tuned = false;
+  bool bulk = false;  // row reductions: bulk-copy pipeline instead of register loads
 };
 
 // Device workspace owned by one fx_expr: reduction partials, tickets,
@@ -51,6 +52,7 @@ struct fx_expr {
   double scal[FX_MAX_SCALARS] = {};
   fx::Workspace ws;
   fx::Workspace ws_tmp;  // unfused intermediates
+  fx::Workspace ws_err;  // error word of bounded waits (kErrTimeout)
   fx::Tune tune;
   int last_launches = 0;
   fx::BatchCache* batch = nullptr;

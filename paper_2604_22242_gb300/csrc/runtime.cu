@@ -210,6 +210,7 @@ fx_status fx_expr_destroy(fx_expr* x) {
   free_batch_cache(x);
   x->ws.release();
   x->ws_tmp.release();
+  x->ws_err.release();
   delete x;
   return FX_OK;
 }
@@ -360,6 +361,20 @@ fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* b
 }
 
 int fx_expr_last_launches(const fx_expr* x) { return x ? x->last_launches : 0; }
+
+fx_status fx_expr_sync_status(fx_expr* x, void* stream) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FX_CUDA(cudaStreamSynchronize(st));
+  FX_CUDA(cudaGetLastError());
+  if (!x->ws_err.p) return FX_OK;
+  unsigned int word = 0;
+  FX_CUDA(cudaMemcpy(&word, x->ws_err.p, sizeof word, cudaMemcpyDeviceToHost));
+  if (word == 0) return FX_OK;
+  FX_CUDA(cudaMemset(x->ws_err.p, 0, sizeof word));
+  return fail(FX_E_CUDA, "a kernel of '%s' gave up a bounded wait for its bulk copies (code %u)",
+              x->e->name, word);
+}
 
 const char* fx_last_error_string(void) { return g_err.c_str(); }
 

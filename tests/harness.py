@@ -165,6 +165,7 @@ def run(fx, name, storage, env, R, C, ldz=None, offset=0, unfused=False, scalars
         else:
             fx.fx_eval(h, sp)
         torch.cuda.synchronize()
+        fx.fx_expr_sync_status(h, sp)   # no bounded wait gave up
         launches = fx.fx_expr_last_launches(h)
         result = {}
         for key, (t, kindk) in outs.items():

@@ -53,6 +53,7 @@ def gpu_grads(fx, storage, env, want=SLOTS, gL=None):
                                  device="cuda")
         fx.fx_eval_backward(h, g_dev.data_ptr() if g_dev is not None else 0, ptrs)
         torch.cuda.synchronize()
+        fx.fx_expr_sync_status(h, 0)
         launches = fx.fx_expr_last_launches(h)
     finally:
         fx.fx_expr_destroy(h)
