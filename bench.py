@@ -21,6 +21,8 @@ no flush between iterations.
                  rows/cols log-uniform in [16, 2048], one graph-replayed launch
   loss8192_f32 / loss8192_bf16     L = accu(square(sigmoid(X%W + b) - Y))
                  forward and fused backward (dX, dW, db)
+  suite10k       the Sec. 4 expressions at 10000^2 FP32: add-N, N = 2..16,
+                 expr1, expr2, relu, sigmoid, swish, gelu
 
 --gpus N: N independent replicas (one process per GPU, torch.distributed.run);
 value = bytes of all ranks / max elapsed time over ranks.
@@ -151,7 +153,8 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
         for k, s in enumerate(ins):
             b = env[s]
             _bind(fx, h, k, d[s], b.rows, b.cols, b.ld)
-            nb += b.rows * b.cols * es
+            if s not in ins[:k]:          # a leaf read twice is read once (fusion)
+                nb += b.rows * b.cols * es
         if kind == "Z":
             o = torch.empty(R * C, dtype=tdt, device=dev)
             _bind(fx, h, len(ins), o, R, C, R)
@@ -206,6 +209,20 @@ def workload(name, fx, torch, dev, sp, keep, size=8192):
                 name == "small1024", storage)
     if name == "batch4096":
         return batch_workload(fx, torch, dev, sp, keep)
+    if name == "suite10k":
+        R = C = 10000
+        env = synth.operands(4, [(f"A{k}", R, C) for k in range(1, 17)], "f32", "uniform")
+        trees = [(f"add{n}", f"add{n}", [f"A{k}" for k in range(1, n + 1)], "Z")
+                 for n in range(2, 17)]
+        trees += [("expr1", "expr1", ["A1", "A2"], "Z"),
+                  ("expr2", "expr2", ["A1", "A2", "A3", "A4"], "Z"),
+                  ("relu", "relu", ["A1"], "Z"), ("sigmoid", "sigmoid", ["A1"], "Z"),
+                  ("swish", "swish", ["A1"], "Z"), ("gelu", "gelu", ["A1"], "Z")]
+        cfg = {"workload": "Sec. 4 suite at 10000x10000 FP32: add-N (N=2..16), expr1, expr2, "
+                           "relu, sigmoid, swish, gelu", "rows": R, "cols": C,
+               "inputs": "A1..A16 U[-1,1], seed 4, column-major",
+               "l2": "inputs larger than L2 (400 MB each), no flush"}
+        return _expr_ops(fx, torch, dev, sp, trees, "f32", env, R, C, keep), cfg, "add16", False, "f32"
     if name in ("loss8192_f32", "loss8192_bf16"):
         return loss_workload(fx, torch, dev, sp, keep, name.split("_")[1])
     raise SystemExit(f"unknown workload {name}")
@@ -547,7 +564,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="expr8192",
                     choices=["expr8192", "expr8192_f64", "small1024", "prec16384_bf16",
-                             "prec16384_f16", "batch4096", "loss8192_f32", "loss8192_bf16"])
+                             "prec16384_f16", "batch4096", "loss8192_f32", "loss8192_bf16",
+                             "suite10k"])
     ap.add_argument("--size", type=int, default=8192, help="rows = cols of the expr8192 trees")
     ap.add_argument("--tune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

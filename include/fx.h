@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FX_MAX_SLOTS 16   /* inputs + outputs of one expression */
+#define FX_MAX_SLOTS 24   /* inputs + outputs of one expression */
 #define FX_MAX_SCALARS 8
 
 typedef struct fx_expr fx_expr; /* opaque; created and destroyed by the library */

@@ -24,7 +24,7 @@ __all__ = [
 ]
 
 FX_F32, FX_F64, FX_BF16, FX_F16 = 0, 1, 2, 3
-FX_MAX_SLOTS = 16
+FX_MAX_SLOTS = 24
 FX_MAX_SCALARS = 8
 KINDS = {0: "elementwise", 1: "full_reduce", 2: "dim_reduce", 3: "multi"}
 TUNE = {"off": 0, "cache": 1, "search": 2}

@@ -33,65 +33,218 @@ struct BatchItem {
   int32_t tile;
 };
 
-template <class T, int V, int KIND> struct batch_epi;
-template <class T, int V> struct batch_epi<T, V, FX_KIND_ELEMENTWISE> {
-  using type = EpiStore<T, V>;
-  static FX_D type make(const BatchMat& m, int zs) { return {static_cast<T*>(const_cast<void*>(m.p[zs])), m.ld[zs]}; }
-};
-template <class T, int V> struct batch_epi<T, V, FX_KIND_MULTI> {
-  using type = EpiStoreSum<T, V>;
-  static FX_D type make(const BatchMat& m, int zs) { return {static_cast<T*>(const_cast<void*>(m.p[zs])), m.ld[zs]}; }
-};
-template <class T, int V> struct batch_epi<T, V, FX_KIND_FULL_REDUCE> {
-  using type = EpiSum<compute_t<T>, V, false>;
-  static FX_D type make(const BatchMat&, int) { return {0}; }
+// ---------------------------------------------------------------- async tile pipeline
+//
+// k_batch_async: each block walks its work items (static stride) with an
+// NBUF-deep pipeline. For the item NBUF-1 ahead, every thread issues
+// asynchronous global->shared copies (cp.async, 4 bytes each, consecutive
+// threads on consecutive elements of a column, so every copy instruction
+// of a warp is coalesced) of the tile's plain leaves (stored column-major,
+// TR rows per column) and transposed leaves (stored as D's columns, TC+1
+// elements per row, so reads in output order avoid bank conflicts); then
+// it waits for the item in front, evaluates the tile from shared memory
+// one element per thread-step, stores Z and reduces. Copies cost shared
+// memory instead of registers, and the item's descriptor is read one
+// item ahead, so the dependent global loads leave the critical path.
+
+namespace cpa {
+FX_D void copy4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tma::saddr(dst)), "l"(src) : "memory");
+}
+FX_D void copy8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tma::saddr(dst)), "l"(src) : "memory");
+}
+FX_D void copy16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tma::saddr(dst)), "l"(src) : "memory");
+}
+FX_D void commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> FX_D void wait_pending() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+template <int B> FX_D void copy(void* dst, const void* src) {
+  if constexpr (B == 4) copy4(dst, src);
+  else if constexpr (B == 8) copy8(dst, src);
+  else {  // 2-byte elements: cp.async moves 4, 8 or 16 bytes, so copy through a register
+    *static_cast<unsigned short*>(dst) = *static_cast<const unsigned short*>(src);
+  }
+}
+}  // namespace cpa
+
+// Per-item fields the evaluation needs, kept per buffer in shared memory.
+struct TileDesc {
+  const void* z;   // output Z (or null)
+  int64_t ldz;
+  int64_t R, C, r0, c0;
+  int64_t item;
+  int32_t mat;
+  int32_t valid;
 };
 
-template <class TS, class T, int KIND, class E>
-FX_D void batch_tile(const E& e, const Slots& sl, const BatchMat& m, int32_t tile, int zs,
-                     double2* part, int64_t it, typename TS::CT* sm) {
-  using Bx = batch_epi<T, TS::V, KIND>;
-  typename Bx::type epi = Bx::make(m, zs);
-  typename Bx::type::State st;
-  st.init();
-  const int64_t tiles_r = (m.rows + TS::TR - 1) / TS::TR;
-  const int64_t tr = tile % tiles_r, tc = tile / tiles_r;
-  tile_body<TS>(e, sl, m.rows, m.cols, tr * TS::TR, tc * TS::TC, epi, st, sm);
-  if constexpr (Bx::type::reduces) {
-    block_merge(st);
-    if (threadIdx.x == 0) part[it] = make_double2(double(st.s), double(st.c));
+// Shared-memory layout of one buffer: plain leaves TC columns of TR rows,
+// transposed leaves TR rows of TC+1 elements.
+template <class LL, int TR, int TC, int I = 0> FX_HD constexpr int abuf_offset() {
+  if constexpr (I == 0) {
+    return 0;
+  } else {
+    using L = typename tl_at<LL, I - 1>::type;
+    constexpr int es = int(sizeof(typename L::elem));
+    constexpr int sz = L::mode == MN ? TR * TC * es : (L::mode == MT ? TR * (TC + 1) * es : 0);
+    return abuf_offset<LL, TR, TC, I - 1>() + ((sz + 15) / 16) * 16;
+  }
+}
+template <class LL, int TR, int TC> FX_HD constexpr int abuf_bytes() {
+  return abuf_offset<LL, TR, TC, tl_size<LL>::value>();
+}
+
+// What issuing one item needs, read from global memory one item early.
+template <int NIN> struct IssueDesc {
+  const void* p[NIN];
+  int64_t ld[NIN];
+  const void* z;
+  int64_t ldz, R, C, r0, c0, item;
+  int32_t mat, vec, valid;
+};
+
+template <int NIN, int TR, int TC, int KIND>
+FX_D IssueDesc<NIN> fetch_item(const BatchMat* mats, const BatchItem* items, int64_t it,
+                               bool valid) {
+  IssueDesc<NIN> d;
+  d.valid = valid ? 1 : 0;
+  if (!valid) return d;
+  const BatchItem w = items[it];
+  const BatchMat& m = mats[w.mat];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) {
+    d.p[k] = m.p[k];
+    d.ld[k] = m.ld[k];
+  }
+  d.z = KIND != FX_KIND_FULL_REDUCE ? m.p[NIN] : nullptr;
+  d.ldz = KIND != FX_KIND_FULL_REDUCE ? m.ld[NIN] : 0;
+  d.R = m.rows;
+  d.C = m.cols;
+  const int64_t tiles_r = (d.R + TR - 1) / TR;
+  d.r0 = (w.tile % tiles_r) * TR;
+  d.c0 = (w.tile / tiles_r) * TC;
+  d.item = it;
+  d.mat = w.mat;
+  d.vec = m.vec;
+  return d;
+}
+
+template <class LL, int TR, int TC, int NT, int NIN, int I = 0>
+FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    T* dst = reinterpret_cast<T*>(buf + abuf_offset<LL, TR, TC, I>());
+    const T* src = static_cast<const T*>(d.p[L::slot]);
+    const int64_t ld = d.ld[L::slot];
+    const int64_t R = d.R, C = d.C, r0 = d.r0, c0 = d.c0;
+    if constexpr (L::mode == MN) {
+      constexpr int W = 16 / int(sizeof(T));  // elements per 16-byte copy
+      if (W > 1 && sizeof(T) >= 4 && d.vec && r0 + TR <= R && c0 + TC <= C) {
+        // a full tile of an aligned matrix: 16-byte copies down each column
+#pragma unroll 2
+        for (int e = threadIdx.x; e < (TR / W) * TC; e += NT) {
+          const int r = (e % (TR / W)) * W, c = e / (TR / W);
+          cpa::copy16(dst + c * TR + r, src + (r0 + r) + (c0 + c) * ld);
+        }
+      } else {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < TR * TC; e += NT) {
+          const int r = e % TR, c = e / TR;
+          if (r0 + r < R && c0 + c < C)
+            cpa::copy<int(sizeof(T))>(dst + c * TR + r, src + (r0 + r) + (c0 + c) * ld);
+        }
+      }
+    } else if constexpr (L::mode == MT) {
+#pragma unroll 4
+      for (int e = threadIdx.x; e < TR * TC; e += NT) {
+        const int c = e % TC, r = e / TC;  // D element (c0 + c, r0 + r)
+        if (r0 + r < R && c0 + c < C)
+          cpa::copy<int(sizeof(T))>(dst + r * (TC + 1) + c, src + (c0 + c) + (r0 + r) * ld);
+      }
+    }
+    issue_tile<LL, TR, TC, NT, NIN, I + 1>(buf, d);
   }
 }
 
-// Matrices whose every full vector is aligned use V-wide tiles, the others
-// scalar tiles; both TR rows high and as wide as two vectors per thread
-// (few registers per thread, so several blocks stay resident per SM).
-template <class E, int V, int TR, int TC, int NT> struct BatchShapes {
-  using Vec = TileShape<E, V, TR, 2 * (NT / (TR / V)), NT>;
-  using One = TileShape<E, 1, TR, 2 * (NT / TR), NT>;
-};
-
-template <class E, class T, int V, int TR, int TC, int NT, int KIND, int NIN>
-__global__ void __launch_bounds__(NT, 3) k_batch(const E e, const BatchMat* __restrict__ mats,
-                                                 const BatchItem* __restrict__ items,
-                                                 const int64_t nitems, double2* part) {
-  using TSv = typename BatchShapes<E, V, TR, TC, NT>::Vec;
-  using TS1 = typename BatchShapes<E, V, TR, TC, NT>::One;
-  using CT = typename TSv::CT;
-  __shared__ CT sm[TSv::SMEM > TS1::SMEM ? TSv::SMEM : TS1::SMEM];
-  for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const BatchItem w = items[it];
-    const BatchMat& m = mats[w.mat];
-    Slots sl;
-#pragma unroll
-    for (int k = 0; k < NIN; ++k) {
-      sl.s[k].p = m.p[k];
-      sl.s[k].ld = m.ld[k];
-      sl.s[k].vs = 1;
+// Element (r, c) of the tile (local indices) of every leaf into a V=1 pack.
+template <class LL, class CT, int TR, int TC, int I = 0>
+FX_D void load_tile_elem(Pack<LL, 1, CT>& p, const char* buf, const BatchMat& m, int64_t r0,
+                         int64_t c0, int r, int c) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    const T* b = reinterpret_cast<const T*>(buf + abuf_offset<LL, TR, TC, I>());
+    if constexpr (L::mode == MN) {
+      pget<I>::of(p).v[0] = b[c * TR + r];
+    } else if constexpr (L::mode == MT) {
+      pget<I>::of(p).v[0] = to_compute<CT>(b[r * (TC + 1) + c]);
+    } else if constexpr (L::mode == MBC) {
+      pget<I>::of(p).v[0] = sload(static_cast<const T*>(m.p[L::slot]) + (r0 + r));
+    } else {
+      pget<I>::of(p).v[0] = sload(static_cast<const T*>(m.p[L::slot]) + (c0 + c));
     }
-    if (m.vec) batch_tile<TSv, T, KIND>(e, sl, m, w.tile, NIN, part, it, sm);
-    else batch_tile<TS1, T, KIND>(e, sl, m, w.tile, NIN, part, it, sm);
+    load_tile_elem<LL, CT, TR, TC, I + 1>(p, buf, m, r0, c0, r, c);
   }
+}
+
+template <class E, class T, int TR, int TC, int NT, int NBUF, int KIND, int NIN>
+__global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* __restrict__ mats,
+                                                    const BatchItem* __restrict__ items,
+                                                    const int64_t nitems, double2* part) {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  constexpr int AB = abuf_bytes<LL, TR, TC>();
+  extern __shared__ __align__(128) char smem[];
+  TileDesc* desc = reinterpret_cast<TileDesc*>(smem + NBUF * AB);
+  const int64_t G = gridDim.x;
+  const int64_t mine = nitems > int64_t(blockIdx.x) ? (nitems - blockIdx.x + G - 1) / G : 0;
+  auto fetch = [&](int64_t j) {
+    return fetch_item<NIN, TR, TC, KIND>(mats, items, blockIdx.x + j * G, j < mine);
+  };
+  // issue a fetched item into buffer b (every thread commits a group, even an empty one)
+  auto issue = [&](const IssueDesc<NIN>& d, int b) {
+    if (d.valid) {
+      issue_tile<LL, TR, TC, NT, NIN>(smem + b * AB, d);
+      if (threadIdx.x == 0)
+        desc[b] = TileDesc{d.z, d.ldz, d.R, d.C, d.r0, d.c0, d.item, d.mat, 1};
+    }
+    cpa::commit();
+  };
+#pragma unroll
+  for (int j = 0; j < NBUF - 1; ++j) issue(fetch(j), j);
+  IssueDesc<NIN> next = fetch(NBUF - 1);
+  for (int64_t j = 0; j < mine; ++j) {
+    issue(next, int((j + NBUF - 1) % NBUF));
+    next = fetch(j + NBUF);  // consumed one iteration later: its loads overlap this tile
+    cpa::wait_pending<NBUF - 1>();
+    __syncthreads();  // every thread's copies of item j have landed; desc visible
+    const int b = int(j % NBUF);
+    const TileDesc d = desc[b];
+    const BatchMat& m = mats[d.mat];
+    ThreadSum<CT> st;
+    st.init();
+    const char* buf = smem + b * AB;
+    for (int q = threadIdx.x; q < TR * TC; q += NT) {
+      const int r = q % TR, c = q / TR;
+      if (d.r0 + r < d.R && d.c0 + c < d.C) {
+        Pack<LL, 1, CT> p;
+        load_tile_elem<LL, CT, TR, TC>(p, buf, m, d.r0, d.c0, r, c);
+        Ctx<LL, 1, CT> cx{p, 0};
+        const CT v = e.ev(cx);
+        if constexpr (KIND != FX_KIND_FULL_REDUCE)
+          sstore(static_cast<T*>(const_cast<void*>(d.z)) + (d.r0 + r) + (d.c0 + c) * d.ldz,
+                 narrow_to<T>::from(v));
+        if constexpr (KIND != FX_KIND_ELEMENTWISE) st.add(v);
+      }
+    }
+    if constexpr (KIND != FX_KIND_ELEMENTWISE) {
+      block_merge(st);
+      if (threadIdx.x == 0) part[d.item] = make_double2(double(st.s), double(st.c));
+    }
+    __syncthreads();  // buffer b is free for the item issued next
+  }
+  cpa::wait_pending<0>();
 }
 
 // One warp per matrix: its tiles' partials, in tile order, summed in FP64.
@@ -196,8 +349,8 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
   using LL = leaves_t<E>;
   using CT = ct_of<E>;
   constexpr int V = vec_width<E, 16>();
-  using TC_ = TileCfg<E, V>;
-  constexpr int TR = TC_::TR, TCc = TC_::TC, NT = TC_::NT;
+  constexpr bool dbl = std::is_same<CT, double>::value;
+  constexpr int TR = dbl ? 32 : 64, TCc = 32, NT = 256, NBUF = 3;
   const int n_in = NIN;
   if constexpr (root_of<Root>::kind == FX_KIND_DIM_REDUCE) {
     return fail(FX_E_UNSUPPORTED, "batched dim reductions are not fused");
@@ -258,9 +411,7 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
         m.rows = R;
         m.cols = C;
         m.vec = vec ? 1 : 0;
-        const int tcm = vec ? BatchShapes<E, V, TR, TCc, NT>::Vec::TC
-                            : BatchShapes<E, V, TR, TCc, NT>::One::TC;
-        const int64_t nt = ((R + TR - 1) / TR) * ((C + tcm - 1) / tcm);
+        const int64_t nt = ((R + TR - 1) / TR) * ((C + TCc - 1) / TCc);
         m.first = int64_t(work.size());
         m.ntiles = int32_t(nt);
         for (int64_t t = 0; t < nt; ++t) work.push_back(BatchItem{int32_t(i), int32_t(t)});
@@ -289,13 +440,18 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
     Run r = run_of(x, st);
     auto launch_all = [&]() -> fx_status {
       if (c.nitems > 0) {
-        auto go = [&](auto kern) -> fx_status {
-          const int grid = grid_for(kern, NT, c.nitems, r.tune);
-          kern<<<grid, NT, 0, st>>>(e, c.mats, c.items, c.nitems, c.part);
-          return after_launch(r, "k_batch");
-        };
         constexpr int KE = kind == FX_KIND_MULTI ? FX_KIND_MULTI : KIND0;
-        FX_TRY(go(k_batch<E, T, V, TR, TCc, NT, KE, NIN>));
+        auto kern = k_batch_async<E, T, TR, TCc, NT, NBUF, KE, NIN>;
+        constexpr int smem = NBUF * abuf_bytes<LL, TR, TCc>() + NBUF * int(sizeof(TileDesc));
+        FX_TRY(allow_smem(kern, smem));
+        const int sms = device_sms() > 0 ? device_sms() : 1;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess || occ < 1) occ = 1;
+        const int bps = r.tune.bps > 0 ? (r.tune.bps < occ ? r.tune.bps : occ) : occ;
+        int64_t grid = int64_t(sms) * bps;
+        if (grid > c.nitems) grid = c.nitems;
+        kern<<<unsigned(grid), NT, smem, st>>>(e, c.mats, c.items, c.nitems, c.part);
+        FX_TRY(after_launch(r, "k_batch_async"));
       }
       if (has_s && c.n > 0) {
         k_batch_combine<CT><<<unsigned((c.n + 7) / 8), 256, 0, st>>>(c.mats, c.n, c.part, sslot);

@@ -6,6 +6,8 @@
 // (fx_expr_set_scalar), s[0], s[1], ..., with the defaults listed.
 #pragma once
 
+#include <utility>
+
 #include "entry.cuh"
 
 namespace fx {
@@ -112,6 +114,130 @@ struct SigmoidSqloss {
   template <class T> static FX_HD auto build(const double*) {
     auto X = in<0, T>(); auto W = in<1, T>(); auto Y = in<2, T>(); auto b = in<3, T>();
     return accu(square(sigmoid(X % W + each_col(b)) - Y));
+  }
+};
+
+// ---------------------------------------------------------------- Sec. 4 suite (FP32)
+//
+// The expressions of the paper's speed comparison. addN: Z = A1 + ... + AN
+// (the add-N bandwidth sweep, N = 2..16; addsub2/addsub4 are add2/add4 on
+// submatrix views, i.e. bindings with the parent's leading dimension).
+
+template <int N, class T, std::size_t... I> FX_HD auto add_fold(std::index_sequence<I...>) {
+  return (... + in<int(I), T>());
+}
+#define FX_ADDN(N, ...)                                                                    \
+  struct Add##N {                                                                          \
+    FX_DEF_COMMON("add" #N, "(+ A1 ... A" #N ")", N, 1, 0, FX_KIND_ELEMENTWISE,            \
+                  dmask(FX_F32), false, false)                                             \
+    static constexpr const char* slots[] = {__VA_ARGS__, "Z"};                             \
+    static constexpr double defaults[] = {0.0};                                            \
+    template <class T> static FX_HD auto build(const double*) {                            \
+      return add_fold<N, T>(std::make_index_sequence<N>{});                                 \
+    }                                                                                      \
+  };
+FX_ADDN(2, "A1", "A2")
+FX_ADDN(3, "A1", "A2", "A3")
+FX_ADDN(4, "A1", "A2", "A3", "A4")
+FX_ADDN(5, "A1", "A2", "A3", "A4", "A5")
+FX_ADDN(6, "A1", "A2", "A3", "A4", "A5", "A6")
+FX_ADDN(7, "A1", "A2", "A3", "A4", "A5", "A6", "A7")
+FX_ADDN(8, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8")
+FX_ADDN(9, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9")
+FX_ADDN(10, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10")
+FX_ADDN(11, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10", "A11")
+FX_ADDN(12, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10", "A11", "A12")
+FX_ADDN(13, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10", "A11", "A12", "A13")
+FX_ADDN(14, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10", "A11", "A12", "A13",
+        "A14")
+FX_ADDN(15, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10", "A11", "A12", "A13",
+        "A14", "A15")
+FX_ADDN(16, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10", "A11", "A12", "A13",
+        "A14", "A15", "A16")
+#undef FX_ADDN
+
+// expr1: Z = 2*(X.t() + Y) + 2*(X + Y.t()), X and Y square
+struct Expr1 {
+  FX_DEF_COMMON("expr1", "(+ (* s0 (+ (t X) Y)) (* s0 (+ X (t Y))))", 2, 1, 1,
+                FX_KIND_ELEMENTWISE, dmask(FX_F32), false, false)
+  static constexpr const char* slots[] = {"X", "Y", "Z"};
+  static constexpr double defaults[] = {2.0};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto X = in<0, T>(); auto Y = in<1, T>();
+    return s[0] * (trans(X) + Y) + s[0] * (X + trans(Y));
+  }
+};
+
+// expr2: Z = a*A + (B + C).t() + log(pow(D, 2)); B and C are cols x rows
+struct Expr2 {
+  FX_DEF_COMMON("expr2", "(+ (+ (* s0 A) (t (+ B C))) (log (pow D s1)))", 4, 1, 2,
+                FX_KIND_ELEMENTWISE, dmask(FX_F32), false, false)
+  static constexpr const char* slots[] = {"A", "B", "C", "D", "Z"};
+  static constexpr double defaults[] = {0.75, 2.0};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto A = in<0, T>(); auto B = in<1, T>(); auto C = in<2, T>(); auto D = in<3, T>();
+    return s[0] * A + trans(B + C) + log(pow(D, s[1]));
+  }
+};
+
+// relu: Z = X % (X > 0)
+struct Relu {
+  FX_DEF_COMMON("relu", "(% X (gt X s0))", 1, 1, 1, FX_KIND_ELEMENTWISE, dmask(FX_F32), false,
+                false)
+  static constexpr const char* slots[] = {"X", "Z"};
+  static constexpr double defaults[] = {0.0};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto X = in<0, T>();
+    return X % (X > s[0]);
+  }
+};
+
+// sigmoid: Z = 1 / (1 + exp(-X)), written out as in the paper's listing of expressions
+struct SigmoidExpr {
+  FX_DEF_COMMON("sigmoid", "(/ s0 (+ s0 (exp (neg X))))", 1, 1, 1, FX_KIND_ELEMENTWISE,
+                dmask(FX_F32), false, false)
+  static constexpr const char* slots[] = {"X", "Z"};
+  static constexpr double defaults[] = {1.0};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto X = in<0, T>();
+    return s[0] / (s[0] + exp(-X));
+  }
+};
+
+// swish: Z = X / (1 + exp(-beta * X))
+struct Swish {
+  FX_DEF_COMMON("swish", "(/ X (+ 1 (exp (neg (* s0 X)))))", 1, 1, 1, FX_KIND_ELEMENTWISE,
+                dmask(FX_F32), false, false)
+  static constexpr const char* slots[] = {"X", "Z"};
+  static constexpr double defaults[] = {1.0};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto X = in<0, T>();
+    return X / (1.0 + exp(-(s[0] * X)));
+  }
+};
+
+// gelu: Z = (X / 2) % (1 + tanh(sqrt(2/pi) * (X + alpha * pow(X, 3))))
+struct Gelu {
+  FX_DEF_COMMON("gelu", "(% (/ X 2) (+ 1 (tanh (* s0 (+ X (* s1 (pow X 3)))))))", 1, 1, 2,
+                FX_KIND_ELEMENTWISE, dmask(FX_F32), false, false)
+  static constexpr const char* slots[] = {"X", "Z"};
+  static constexpr double defaults[] = {0.7978845608028654, 0.044715};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto X = in<0, T>();
+    return (X / 2.0) % (1.0 + tanh(s[0] * (X + s[1] * pow(X, 3.0))));
+  }
+};
+
+// (A + B) % (C + D): diagsum when bound to the diagonal views X.diag(-1),
+// X.diag(1), Y.diag(-1), Y.diag(1) (1 x n leaves with ld = parent ld + 1)
+struct SumSchur {
+  FX_DEF_COMMON("sum_schur", "(% (+ A B) (+ C D))", 4, 1, 0, FX_KIND_ELEMENTWISE,
+                dmask(FX_F32), false, false)
+  static constexpr const char* slots[] = {"A", "B", "C", "D", "Z"};
+  static constexpr double defaults[] = {0.0};
+  template <class T> static FX_HD auto build(const double*) {
+    auto A = in<0, T>(); auto B = in<1, T>(); auto C = in<2, T>(); auto D = in<3, T>();
+    return (A + B) % (C + D);
   }
 };
 

@@ -70,10 +70,14 @@ struct OpDiv {
     db = -a / (b * b);
   }
 };
-struct OpPow {  // a ^ b (b is a scalar in the trees built here)
-  template <class C> static FX_D C f(C a, C b) { return m_pow(a, b); }
+struct OpPow {  // a ^ b (b is a scalar in the trees built here; 2 and 3 by multiplication)
+  template <class C> static FX_D C f(C a, C b) {
+    if (b == C(2)) return a * a;
+    if (b == C(3)) return a * a * a;
+    return m_pow(a, b);
+  }
   template <class C> static FX_D void d(C a, C b, C& da, C& db) {
-    da = b * m_pow(a, b - C(1));
+    da = b == C(2) ? C(2) * a : (b == C(3) ? C(3) * a * a : b * m_pow(a, b - C(1)));
     db = C(0);
   }
 };

@@ -236,16 +236,22 @@ fx_status launch_flat_u(const Run& r, const E& e, const Slots& sl, int64_t n, co
   return after_launch(r, "k_flat");
 }
 
+// Vectors per leaf in flight per thread: at most 16 vectors in all (the
+// register budget of a thread), so 8 for one or two leaves, 4 for up to
+// four, 2 for up to eight, 1 beyond.
+template <class E> constexpr int max_unroll() {
+  constexpr int nl = tl_size<leaves_t<E>>::value;
+  return nl <= 2 ? 8 : (nl <= 4 ? 4 : (nl <= 8 ? 2 : 1));
+}
+
 template <class E, class Epi, int V>
 fx_status launch_flat(const Run& r, const E& e, const Slots& sl, int64_t n, const Epi& epi,
                       RedArgs red, int64_t flat_rows) {
+  constexpr int UM = max_unroll<E>();
   switch (r.tune.unroll) {
-    case 2: return launch_flat_u<E, Epi, V, 2>(r, e, sl, n, epi, red, flat_rows);
-    case 8: {  // 8 vectors per leaf in flight only for trees of at most two leaves
-      constexpr int U8 = tl_size<leaves_t<E>>::value <= 2 ? 8 : 4;
-      return launch_flat_u<E, Epi, V, U8>(r, e, sl, n, epi, red, flat_rows);
-    }
-    default: return launch_flat_u<E, Epi, V, 4>(r, e, sl, n, epi, red, flat_rows);
+    case 2: return launch_flat_u<E, Epi, V, (2 < UM ? 2 : UM)>(r, e, sl, n, epi, red, flat_rows);
+    case 8: return launch_flat_u<E, Epi, V, UM>(r, e, sl, n, epi, red, flat_rows);
+    default: return launch_flat_u<E, Epi, V, (4 < UM ? 4 : UM)>(r, e, sl, n, epi, red, flat_rows);
   }
 }
 

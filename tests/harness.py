@@ -31,9 +31,22 @@ TREES = {
     "diff_norm": "(norm (- X Y))",
     "schur_trans_accu": "(+ (% A B) (* {s0} (t C)))",
     "sigmoid_sqloss": "(accu (square (- (sigmoid (+ (% X W) (each_col b))) Y)))",
+    "expr1": "(+ (* {s0} (+ (t X) Y)) (* {s0} (+ X (t Y))))",
+    "expr2": "(+ (+ (* {s0} A) (t (+ B C))) (log (pow D {s1})))",
+    "relu": "(% X (gt X {s0}))",
+    "sigmoid": "(/ {s0} (+ {s0} (exp (neg X))))",
+    "swish": "(/ X (+ 1 (exp (neg (* {s0} X)))))",
+    "gelu": "(% (/ X 2) (+ 1 (tanh (* {s0} (+ X (* {s1} (pow X 3)))))))",
+    "sum_schur": "(% (+ A B) (+ C D))",
 }
+for _n in range(2, 17):
+    _t = "A1"
+    for _k in range(2, _n + 1):
+        _t = f"(+ {_t} A{_k})"
+    TREES[f"add{_n}"] = _t
 DEFAULT_SCALARS = {"schur_exp_trans": [3.5], "schur_sqrt_sigmoid": [1.0],
-                   "schur_trans_accu": [0.5]}
+                   "schur_trans_accu": [0.5], "expr1": [2.0], "expr2": [0.75, 2.0], "relu": [0.0],
+                   "sigmoid": [1.0], "swish": [1.0], "gelu": [0.7978845608028654, 0.044715]}
 SLOTS = {
     "schur_exp_trans": ["A", "B", "C", "D"],
     "sqdiff_accu": ["A", "B"],
@@ -43,8 +56,12 @@ SLOTS = {
     "diff_norm": ["X", "Y"],
     "schur_trans_accu": ["A", "B", "C"],
     "sigmoid_sqloss": ["X", "W", "Y", "b"],
+    "expr1": ["X", "Y"], "expr2": ["A", "B", "C", "D"], "relu": ["X"], "sigmoid": ["X"],
+    "swish": ["X"], "gelu": ["X"], "sum_schur": ["A", "B", "C", "D"],
 }
-TRANSPOSED = {"schur_exp_trans": {"D"}, "schur_trans_accu": {"C"}}
+for _n in range(2, 17):
+    SLOTS[f"add{_n}"] = [f"A{_k}" for _k in range(1, _n + 1)]
+TRANSPOSED = {"schur_exp_trans": {"D"}, "schur_trans_accu": {"C"}, "expr2": {"B", "C"}}
 VECTORS = {"sigmoid_sqloss": {"b"}}
 
 TOL_EW = {"f64": 1e-13, "f32": 2e-6, "bf16": 8e-3, "f16": 1e-3}
@@ -52,7 +69,8 @@ TOL_TRANS = {"f64": 1e-13, "f32": 1e-5, "bf16": 8e-3, "f16": 1e-3}
 # reductions of every storage type come out in FP32 (FP64 for f64) from a
 # compensated FP32 accumulation, so they are held to the FP32 reduction bound
 TOL_RED = {"f64": 1e-13, "f32": 1e-5, "bf16": 1e-5, "f16": 1e-5}
-HAS_TRANSCENDENTAL = {"schur_exp_trans", "schur_sqrt_sigmoid", "sigmoid_sqloss"}
+HAS_TRANSCENDENTAL = {"schur_exp_trans", "schur_sqrt_sigmoid", "sigmoid_sqloss", "expr2",
+                      "sigmoid", "swish", "gelu"}
 
 
 def tree_of(name, scalars=None):

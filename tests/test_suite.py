@@ -1,0 +1,91 @@
+"""The Sec. 4 expression suite on the fused path (GPU): add-N for N = 2..16,
+expr1, expr2, relu, sigmoid, swish, gelu, and the view-based cases
+addsub2/addsub4 (submatrix leaves) and diagsum (diagonal leaves)."""
+import numpy as np
+import pytest
+
+import synth
+from harness import oracle_outputs, run, scaled_error, specs_for, tolerance
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1), (33, 17), (64, 64), (100, 37), (257, 129)]
+SQUARE = [(1, 1), (33, 33), (64, 64), (100, 100), (257, 257)]
+
+
+@pytest.fixture(scope="module")
+def fx(fxlib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return fxlib
+
+
+def check(name, got, env, label, scalars=None):
+    for key, (rv, rs) in oracle_outputs(name, env, scalars).items():
+        tol = tolerance(name, "f32", key)
+        err, _, bad, _ = scaled_error(got[key], rv, rs, "f32")
+        assert bad == 0, f"{name}{label}: {bad} wrong non-finite outputs"
+        assert err <= tol, f"{name}{label}: scaled error {err:.3e} > {tol:.1e}"
+
+
+@pytest.mark.parametrize("n", list(range(2, 17)))
+def test_add_n(fx, n):
+    name = f"add{n}"
+    for R, C in SHAPES:
+        env = synth.operands(40 + n, specs_for(name, R, C), "f32", "uniform")
+        got = run(fx, name, "f32", env, R, C)
+        check(name, got, env, f" at {R}x{C}")
+        assert got["_launches"] == 1
+
+
+@pytest.mark.parametrize("name", ["expr1", "expr2", "relu", "sigmoid", "swish", "gelu"])
+def test_suite_expressions(fx, name):
+    shapes = SQUARE if name == "expr1" else SHAPES
+    for R, C in shapes:
+        env = synth.operands(50, specs_for(name, R, C), "f32", "normal")
+        got = run(fx, name, "f32", env, R, C)
+        check(name, got, env, f" at {R}x{C}")
+
+
+def _submatrix(parent, r0, c0, rows, cols):
+    """A view of `parent` (a synth.Buffer): pointer offset, the parent's ld."""
+    off = r0 + c0 * parent.ld
+    return synth.Buffer(parent.data[off:], rows, cols, parent.ld, parent.storage)
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_addsub_views(fx, n):
+    # the centre of each matrix with half the rows and columns
+    P = 96
+    parents = synth.operands(60, [(f"A{k}", P, P) for k in range(1, n + 1)], "f32", "uniform")
+    env = {k: _submatrix(b, P // 4, P // 4, P // 2, P // 2) for k, b in parents.items()}
+    got = run(fx, f"add{n}", "f32", env, P // 2, P // 2)
+    check(f"add{n}", got, env, " (centre submatrices)")
+
+
+def test_diagsum_views(fx):
+    # (X.diag(-1) + X.diag(1)) % (Y.diag(-1) + Y.diag(1)) as 1 x (n-1) leaves
+    n = 130
+    XY = synth.operands(61, [("X", n, n), ("Y", n, n)], "f32", "normal")
+
+    def diag(b, k):
+        off = -k if k < 0 else k * b.ld      # element (-k, 0) or (0, k)
+        return synth.Buffer(b.data[off:], 1, n - 1, b.ld + 1, b.storage)
+
+    env = {"A": diag(XY["X"], -1), "B": diag(XY["X"], 1), "C": diag(XY["Y"], -1),
+           "D": diag(XY["Y"], 1)}
+    got = run(fx, "sum_schur", "f32", env, 1, n - 1)
+    check("sum_schur", got, env, " (diagonal views)")
+    X = XY["X"].f64().reshape(n, n).T
+    Y = XY["Y"].f64().reshape(n, n).T
+    want = (np.diag(X, -1) + np.diag(X, 1)) * (np.diag(Y, -1) + np.diag(Y, 1))
+    assert np.allclose(got["Z"][0], want, rtol=1e-6, atol=1e-6)
+
+
+def test_unfused_suite(fx):
+    for name in ["add8", "expr1", "expr2", "gelu"]:
+        R = C = 64
+        env = synth.operands(62, specs_for(name, R, C), "f32", "normal")
+        got = run(fx, name, "f32", env, R, C, unfused=True)
+        check(name, got, env, " (unfused)")
