@@ -178,7 +178,7 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
     return ops
 
 
-def workload(name, fx, torch, dev, sp, keep, size=8192):
+def workload(name, fx, torch, dev, sp, keep, size=8192, count=4096):
     """(ops, config dict, dominant op key, flush_l2, dtype) for a workload."""
     import numpy as np
     import synth
@@ -197,7 +197,7 @@ def workload(name, fx, torch, dev, sp, keep, size=8192):
         return _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep), cfg, "Z", False, storage
     if name in ("small1024", "prec16384_bf16", "prec16384_f16"):
         storage = "f32" if name == "small1024" else name.split("_")[1]
-        R = C = 1024 if name == "small1024" else 16384
+        R = C = (1024 if name == "small1024" else 16384) if size == 8192 else size
         dist = "uniform" if name == "small1024" else "lognormal_signed"
         env = synth.operands(0, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], storage, dist)
         trees = [("schur_exp_trans", "Z", "ABCD", "Z"), ("sqdiff_accu", "s", "AB", "s")]
@@ -208,7 +208,7 @@ def workload(name, fx, torch, dev, sp, keep, size=8192):
         return (_expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep), cfg, "Z",
                 name == "small1024", storage)
     if name == "batch4096":
-        return batch_workload(fx, torch, dev, sp, keep)
+        return batch_workload(fx, torch, dev, sp, keep, count)
     if name == "suite10k":
         R = C = 10000
         env = synth.operands(4, [(f"A{k}", R, C) for k in range(1, 17)], "f32", "uniform")
@@ -224,14 +224,14 @@ def workload(name, fx, torch, dev, sp, keep, size=8192):
                "l2": "inputs larger than L2 (400 MB each), no flush"}
         return _expr_ops(fx, torch, dev, sp, trees, "f32", env, R, C, keep), cfg, "add16", False, "f32"
     if name in ("loss8192_f32", "loss8192_bf16"):
-        return loss_workload(fx, torch, dev, sp, keep, name.split("_")[1])
+        return loss_workload(fx, torch, dev, sp, keep, name.split("_")[1], size)
     raise SystemExit(f"unknown workload {name}")
 
 
-def batch_workload(fx, torch, dev, sp, keep):
+def batch_workload(fx, torch, dev, sp, keep, count=4096):
     import numpy as np
     import synth
-    rows, cols, ops_ = synth.batch_operands(2, 4096, [("A", False), ("B", False), ("C", True)])
+    rows, cols, ops_ = synth.batch_operands(2, count, [("A", False), ("B", False), ("C", True)])
     n = len(rows)
 
     def arena(mats):
@@ -286,16 +286,16 @@ def batch_workload(fx, torch, dev, sp, keep):
 
     op = Op("batch", nbytes, lambda: fx.fx_eval_batch(h, items, sp, True), unfused,
             lambda: fx.fx_expr_last_launches(h))
-    cfg = {"workload": "Z=A%B+0.5*trans(C), s=accu(Z) over 4096 matrices, rows/cols "
+    cfg = {"workload": f"Z=A%B+0.5*trans(C), s=accu(Z) over {n} matrices, rows/cols "
                        "log-uniform [16,2048] seed 2", "matrices": n, "elements": nel,
            "l2": "working set 11.5 GB, no flush", "graph": True}
     return [op], cfg, "batch", False, "f32"
 
 
-def loss_workload(fx, torch, dev, sp, keep, storage):
+def loss_workload(fx, torch, dev, sp, keep, storage, size=8192):
     import numpy as np
     import synth
-    R = C = 8192
+    R = C = size
     env = synth.operands(3, [("X", R, C), ("W", R, C), ("Y", R, C), ("b", R, 1)], storage,
                          "normal_half")
     tdt = torch.float32 if storage == "f32" else torch.bfloat16
@@ -323,9 +323,23 @@ def loss_workload(fx, torch, dev, sp, keep, storage):
            Op("backward", bwd_bytes, lambda: fx.fx_eval_backward(h, 0, ptrs, sp), None,
               lambda: fx.fx_expr_last_launches(h))]
     cfg = {"workload": f"L=accu(square(sigmoid(X%W+b.each_col)-Y)) forward and backward (dX,dW,db), "
-                       f"8192x8192 {storage}", "rows": R, "cols": C,
+                       f"{R}x{C} {storage}", "rows": R, "cols": C,
            "inputs": "X,W,Y,b N(0, sd 0.5), seed 3", "l2": "inputs larger than L2, no flush"}
     return ops, cfg, "backward", False, storage
+
+
+# ---------------------------------------------------------------- ranks
+
+def aggregate(ms_local, step_bytes, steps, world, dist=None, device="cpu"):
+    """Whole-job timing over replicas: the slowest rank's timed region
+    (max over ranks) and the bytes of all ranks over that time (GB/s)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * step_bytes * steps / (ms / 1e3) / 1e9
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -396,11 +410,17 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(device=dev)
     sp = int(stream.cuda_stream)
     keep = {}
-    ops, cfg, dom, flush, storage = workload(args.workload, fx, torch, dev, sp, keep, args.size)
+    ops, cfg, dom, flush, storage = workload(args.workload, fx, torch, dev, sp, keep, args.size,
+                                            args.count)
+    handles = [val[0] for key, val in keep.items()
+               if isinstance(val, tuple) and len(val) == 2 and key in [o.key for o in ops]]
+    if args.shape:
+        cfg["launch_shape"] = args.shape
+        for h in handles:
+            fx.fx_expr_set_launch_shape(h, *[int(v) for v in args.shape.split(",")])
     if args.tune:
-        for key, val in keep.items():
-            if isinstance(val, tuple) and len(val) == 2 and key in [o.key for o in ops]:
-                fx.fx_tune(val[0], "search", sp)
+        for h in handles:
+            fx.fx_tune(h, "search", sp)
     flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
     torch.cuda.synchronize()
     step_bytes = sum(o.bytes for o in ops)
@@ -472,14 +492,10 @@ def run_ours(args, rank, world):
             e2e = e2e_run(fx, torch, stream, sp, keep, storage, K, args.size)
 
     fused_u = sum(per_ms[k] for k in u_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = aggregate(ms, step_bytes, K, world, dist, device=dev)
     if rank != 0:
         return
     peak, peak_kind = measured_peak()
-    value = world * step_bytes * K / (ms / 1e3) / 1e9
     dom_op = next(o for o in ops if o.key == dom)
     z_gbs = dom_op.bytes / (per_ms[dom] / 1e3) / 1e9
     tr = TRAFFIC.get((args.workload, dom))
@@ -566,8 +582,12 @@ def main():
                     choices=["expr8192", "expr8192_f64", "small1024", "prec16384_bf16",
                              "prec16384_f16", "batch4096", "loss8192_f32", "loss8192_bf16",
                              "suite10k"])
-    ap.add_argument("--size", type=int, default=8192, help="rows = cols of the expr8192 trees")
+    ap.add_argument("--size", type=int, default=8192,
+                    help="rows = cols of the expr8192 and loss8192 workloads")
+    ap.add_argument("--count", type=int, default=4096, help="matrices of the batch4096 workload")
     ap.add_argument("--tune", action="store_true", help="autotune launch shapes first")
+    ap.add_argument("--shape", default="",
+                    help="fixed launch shape block,unroll,blocks_per_sm,pipeline for every tree")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-cols", type=int, default=4096)
     ap.add_argument("--ref-cols", type=int, default=512)

@@ -181,8 +181,24 @@ fx_status fx_eval_backward(fx_expr* x, const void* grad_out, void* const* grad_p
 fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream);
 
 /* Launch shape currently chosen (for reports): threads per block, vectors
- * per thread per step, blocks per SM. */
-fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* blocks_per_sm);
+ * per thread per step, blocks per SM (0: as many as fit), and the kernel
+ * variant (0: register loads; 1: copy pipeline, see
+ * fx_expr_set_launch_shape). Null pointers are skipped. */
+fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* blocks_per_sm,
+                               int* pipeline);
+
+/* Fixes the launch shape (what FX_TUNE_SEARCH would choose) until the next
+ * fx_tune call. block: threads per block of the streaming kernels, a
+ * multiple of 32 in [64, 512]; unroll: 2, 4 or 8 vectors per thread per
+ * step; blocks_per_sm: 0 (as many as fit) to 32; pipeline: 0 for the
+ * register-load kernels, 1 for the copy-pipeline variants where a tree has
+ * one (trees with transposed leaves stage their tiles through a cp.async
+ * ring; sum/max along dim 1 is fed by bulk copies), used only when the
+ * operands meet that variant's alignment rules. Results are the same
+ * within each kernel's rounding rules; the choice changes speed only.
+ * FX_E_ARG for a value out of range (the shape is then unchanged). */
+fx_status fx_expr_set_launch_shape(fx_expr* x, int block, int unroll, int blocks_per_sm,
+                                   int pipeline);
 
 /* Number of kernel launches the last evaluation call on this object
  * enqueued (for launch accounting). */

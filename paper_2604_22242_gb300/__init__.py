@@ -19,6 +19,7 @@ __all__ = [
     "fx_list", "fx_expr_create", "fx_expr_destroy", "fx_expr_info", "fx_expr_slot_name",
     "fx_expr_bind", "fx_expr_set_scalar", "fx_expr_get_scalar", "fx_eval", "fx_eval_unfused",
     "fx_eval_host", "fx_eval_batch", "fx_eval_backward", "fx_tune", "fx_expr_launch_shape",
+    "fx_expr_set_launch_shape",
     "fx_expr_last_launches", "fx_expr_sync_status", "fx_last_error_string", "fx_status_string", "BatchItem",
     "colmajor", "bind_tensor", "Expr", "FusedLoss", "DTYPE_OF",
 ]
@@ -77,7 +78,8 @@ def lib():
         "fx_eval_backward": (st, [vp, vp, pp, vp]),
         "fx_tune": (st, [vp, i32, vp]),
         "fx_expr_launch_shape": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                      ctypes.POINTER(i32)]),
+                                      ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "fx_expr_set_launch_shape": (st, [vp, i32, i32, i32, i32]),
         "fx_expr_last_launches": (i32, [vp]),
         "fx_expr_sync_status": (st, [vp, vp]),
         "fx_last_error_string": (ctypes.c_char_p, []),
@@ -180,9 +182,16 @@ def fx_tune(h, mode: str = "search", stream: int = 0):
 
 
 def fx_expr_launch_shape(h):
-    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().fx_expr_launch_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return a.value, b.value, c.value
+    """(block, unroll, blocks_per_sm, pipeline) currently in force."""
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().fx_expr_launch_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                      ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def fx_expr_set_launch_shape(h, block: int, unroll: int, blocks_per_sm: int = 0,
+                             pipeline: int = 0):
+    _check(lib().fx_expr_set_launch_shape(h, block, unroll, blocks_per_sm, pipeline))
 
 
 def fx_expr_last_launches(h) -> int:

@@ -47,26 +47,6 @@ struct BatchItem {
 // memory instead of registers, and the item's descriptor is read one
 // item ahead, so the dependent global loads leave the critical path.
 
-namespace cpa {
-FX_D void copy4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tma::saddr(dst)), "l"(src) : "memory");
-}
-FX_D void copy8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tma::saddr(dst)), "l"(src) : "memory");
-}
-FX_D void copy16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tma::saddr(dst)), "l"(src) : "memory");
-}
-FX_D void commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> FX_D void wait_pending() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-template <int B> FX_D void copy(void* dst, const void* src) {
-  if constexpr (B == 4) copy4(dst, src);
-  else if constexpr (B == 8) copy8(dst, src);
-  else {  // 2-byte elements: cp.async moves 4, 8 or 16 bytes, so copy through a register
-    *static_cast<unsigned short*>(dst) = *static_cast<const unsigned short*>(src);
-  }
-}
-}  // namespace cpa
 
 // Per-item fields the evaluation needs, kept per buffer in shared memory.
 struct TileDesc {
@@ -129,41 +109,53 @@ FX_D IssueDesc<NIN> fetch_item(const BatchMat* mats, const BatchItem* items, int
   return d;
 }
 
+// Thread t copies rows (t % TR) [+W-blocks] of columns t / TR, t / TR + NT/TR, ...
+// of each plain leaf, and elements (t % TC) of D's columns t / TC, ... of
+// each transposed leaf; interior tiles skip every bounds test. Offsets are
+// 32-bit: a batch matrix holds fewer than 2^31 elements.
 template <class LL, int TR, int TC, int NT, int NIN, int I = 0>
-FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d) {
+FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d, bool full) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
     using T = typename L::elem;
     T* dst = reinterpret_cast<T*>(buf + abuf_offset<LL, TR, TC, I>());
-    const T* src = static_cast<const T*>(d.p[L::slot]);
-    const int64_t ld = d.ld[L::slot];
-    const int64_t R = d.R, C = d.C, r0 = d.r0, c0 = d.c0;
+    const int ld = int(d.ld[L::slot]);
+    const int rr = int(d.R - d.r0), cc = int(d.C - d.c0);  // rows / cols left in the matrix
     if constexpr (L::mode == MN) {
+      const T* src = static_cast<const T*>(d.p[L::slot]) + d.r0 + d.c0 * int64_t(ld);
       constexpr int W = 16 / int(sizeof(T));  // elements per 16-byte copy
-      if (W > 1 && sizeof(T) >= 4 && d.vec && r0 + TR <= R && c0 + TC <= C) {
-        // a full tile of an aligned matrix: 16-byte copies down each column
-#pragma unroll 2
-        for (int e = threadIdx.x; e < (TR / W) * TC; e += NT) {
-          const int r = (e % (TR / W)) * W, c = e / (TR / W);
-          cpa::copy16(dst + c * TR + r, src + (r0 + r) + (c0 + c) * ld);
-        }
+      if (W > 1 && sizeof(T) >= 4 && d.vec && full) {
+        static_assert((TR / W) * TC % NT == 0 && NT % (TR / W) == 0, "vector copy shape");
+        const int r = (threadIdx.x % (TR / W)) * W;
+#pragma unroll
+        for (int c = threadIdx.x / (TR / W); c < TC; c += NT / (TR / W))
+          cpa::copy16(dst + c * TR + r, src + r + c * ld);
       } else {
-#pragma unroll 4
-        for (int e = threadIdx.x; e < TR * TC; e += NT) {
-          const int r = e % TR, c = e / TR;
-          if (r0 + r < R && c0 + c < C)
-            cpa::copy<int(sizeof(T))>(dst + c * TR + r, src + (r0 + r) + (c0 + c) * ld);
+        static_assert(NT % TR == 0, "scalar copy shape");
+        const int r = threadIdx.x % TR;
+        if (full) {
+#pragma unroll
+          for (int c = threadIdx.x / TR; c < TC; c += NT / TR)
+            cpa::copy<int(sizeof(T))>(dst + c * TR + r, src + r + c * ld);
+        } else if (r < rr) {
+          for (int c = threadIdx.x / TR; c < TC && c < cc; c += NT / TR)
+            cpa::copy<int(sizeof(T))>(dst + c * TR + r, src + r + c * ld);
         }
       }
     } else if constexpr (L::mode == MT) {
-#pragma unroll 4
-      for (int e = threadIdx.x; e < TR * TC; e += NT) {
-        const int c = e % TC, r = e / TC;  // D element (c0 + c, r0 + r)
-        if (r0 + r < R && c0 + c < C)
-          cpa::copy<int(sizeof(T))>(dst + r * (TC + 1) + c, src + (c0 + c) + (r0 + r) * ld);
+      static_assert(NT % TC == 0, "transposed copy shape");
+      const T* src = static_cast<const T*>(d.p[L::slot]) + d.c0 + d.r0 * int64_t(ld);
+      const int c = threadIdx.x % TC;  // D element (c0 + c, r0 + r)
+      if (full) {
+#pragma unroll
+        for (int r = threadIdx.x / TC; r < TR; r += NT / TC)
+          cpa::copy<int(sizeof(T))>(dst + r * (TC + 1) + c, src + c + r * ld);
+      } else if (c < cc) {
+        for (int r = threadIdx.x / TC; r < TR && r < rr; r += NT / TC)
+          cpa::copy<int(sizeof(T))>(dst + r * (TC + 1) + c, src + c + r * ld);
       }
     }
-    issue_tile<LL, TR, TC, NT, NIN, I + 1>(buf, d);
+    issue_tile<LL, TR, TC, NT, NIN, I + 1>(buf, d, full);
   }
 }
 
@@ -205,7 +197,8 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
   // issue a fetched item into buffer b (every thread commits a group, even an empty one)
   auto issue = [&](const IssueDesc<NIN>& d, int b) {
     if (d.valid) {
-      issue_tile<LL, TR, TC, NT, NIN>(smem + b * AB, d);
+      const bool full = d.r0 + TR <= d.R && d.c0 + TC <= d.C;
+      issue_tile<LL, TR, TC, NT, NIN>(smem + b * AB, d, full);
       if (threadIdx.x == 0)
         desc[b] = TileDesc{d.z, d.ldz, d.R, d.C, d.r0, d.c0, d.item, d.mat, 1};
     }
@@ -222,23 +215,33 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
     const int b = int(j % NBUF);
     const TileDesc d = desc[b];
     const BatchMat& m = mats[d.mat];
-    ThreadSum<CT> st;
-    st.init();
+    // a thread adds at most TC*TR/NT values of a tile: a plain sum; the block
+    // merge across threads and the per-matrix combine are compensated
+    CT tsum = CT(0);
     const char* buf = smem + b * AB;
-    for (int q = threadIdx.x; q < TR * TC; q += NT) {
-      const int r = q % TR, c = q / TR;
-      if (d.r0 + r < d.R && d.c0 + c < d.C) {
-        Pack<LL, 1, CT> p;
-        load_tile_elem<LL, CT, TR, TC>(p, buf, m, d.r0, d.c0, r, c);
-        Ctx<LL, 1, CT> cx{p, 0};
-        const CT v = e.ev(cx);
-        if constexpr (KIND != FX_KIND_FULL_REDUCE)
-          sstore(static_cast<T*>(const_cast<void*>(d.z)) + (d.r0 + r) + (d.c0 + c) * d.ldz,
-                 narrow_to<T>::from(v));
-        if constexpr (KIND != FX_KIND_ELEMENTWISE) st.add(v);
+    const int r = threadIdx.x % TR;
+    const int rr = int(d.R - d.r0), cc = int(d.C - d.c0);
+    T* z = KIND != FX_KIND_FULL_REDUCE
+               ? static_cast<T*>(const_cast<void*>(d.z)) + d.r0 + d.c0 * d.ldz
+               : nullptr;
+    const int ldz = int(d.ldz);
+    if (r < rr) {
+#pragma unroll 4
+      for (int c = threadIdx.x / TR; c < TC; c += NT / TR) {
+        if (c < cc) {
+          Pack<LL, 1, CT> p;
+          load_tile_elem<LL, CT, TR, TC>(p, buf, m, d.r0, d.c0, r, c);
+          Ctx<LL, 1, CT> cx{p, 0};
+          const CT v = e.ev(cx);
+          if constexpr (KIND != FX_KIND_FULL_REDUCE) sstore(z + r + c * ldz, narrow_to<T>::from(v));
+          if constexpr (KIND != FX_KIND_ELEMENTWISE) tsum += v;
+        }
       }
     }
     if constexpr (KIND != FX_KIND_ELEMENTWISE) {
+      std::conditional_t<std::is_same<CT, double>::value, PlainSum<CT>, CompSum<CT>> st;
+      st.s = tsum;
+      st.c = CT(0);
       block_merge(st);
       if (threadIdx.x == 0) part[d.item] = make_double2(double(st.s), double(st.c));
     }

@@ -32,7 +32,7 @@ inline std::string tune_key(const fx_expr* x) {
   return buf;
 }
 
-inline fx_status run_tune(fx_expr* x, int mode, cudaStream_t st, EvalFn ev) {
+inline fx_status run_tune(fx_expr* x, int mode, cudaStream_t st, EvalFn ev, int npipe) {
   const std::string key = tune_key(x);
   if (mode == FX_TUNE_CACHE) {
     Tune t;
@@ -48,10 +48,11 @@ inline fx_status run_tune(fx_expr* x, int mode, cudaStream_t st, EvalFn ev) {
   Tune best{};
   float best_ms = 1e30f;
   fx_status status = FX_OK;
+  for (int pi = 0; pi < npipe; ++pi)
   for (int bl : blocks)
     for (int un : unrolls)
       for (int bp : bpss) {
-        x->tune = Tune{bl, un, bp, true};
+        x->tune = Tune{bl, un, bp, true, pi};
         for (int w = 0; w < 2 && status == FX_OK; ++w) status = ev(x, st);
         if (status != FX_OK) break;
         cudaEventRecord(a, st);
@@ -93,7 +94,14 @@ template <class Def, class T> struct Inst {
     if constexpr (Def::batchable) return run_batch<T, Def::n_in, Def::kind>(x, root(x), n, it, st, g);
     else return fail(FX_E_UNSUPPORTED, "no batched entry");
   }
-  static fx_status tune(fx_expr* x, int mode, cudaStream_t st) { return run_tune(x, mode, st, &eval); }
+  // Trees with transposed leaves and row reductions have a copy-pipeline
+  // variant; the search times both.
+  static fx_status tune(fx_expr* x, int mode, cudaStream_t st) {
+    using R0 = std::decay_t<decltype(root(x))>;
+    constexpr bool pv =
+        root_of<R0>::kind == FX_KIND_DIM_REDUCE || count_mt<leaves_t<typename root_of<R0>::inner>>() > 0;
+    return run_tune(x, mode, st, &eval, pv ? 2 : 1);
+  }
   static Entry entry() {
     return Entry{Def::name, Def::formula, dtype_of<T>::value, Def::n_in, Def::n_out, Def::n_scal,
                  fx_kind(Def::kind), Def::slots, Def::defaults, &eval, &unfused,

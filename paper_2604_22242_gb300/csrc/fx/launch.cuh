@@ -6,7 +6,7 @@
 #include <cmath>
 #include <string>
 
-#include "bulk.cuh"
+#include "async.cuh"
 #include "runtime.hpp"
 
 namespace fx {
@@ -277,6 +277,64 @@ fx_status launch_tile(const Run& r, const E& e, const Slots& sl, int64_t R, int6
   return after_launch(r, "k_tile");
 }
 
+// Transposed leaves of 2-byte types are copied in element pairs: 4-byte
+// aligned base, even leading dimension.
+template <class LL, int I = 0> bool mt_pairs_ok(const Binding* b) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    if constexpr (L::mode == MT && sizeof(typename L::elem) == 2) {
+      const Binding& x = b[L::slot];
+      if (!aligned(x.p, 4) || x.ld % 2 != 0) return false;
+    }
+    return mt_pairs_ok<LL, I + 1>(b);
+  }
+  return true;
+}
+
+// k_tile_async shapes: 64 x 64 tiles for 2-byte types, 64 x 32 for 4-byte,
+// 32 x 32 for 8-byte; three stages.
+template <class E, int V> struct TileAsyncCfg {
+  static constexpr int es = tl_max_elem<leaves_t<E>>::value;
+  static constexpr int TR = es == 8 ? 32 : 64;
+  static constexpr int TC = es == 2 ? 64 : 32;
+  static constexpr int NT = 256, NBUF = 3;
+  static constexpr int SMEM = NBUF * tbuf_offset<leaves_t<E>, TR, TC, tl_size<leaves_t<E>>::value>();
+};
+
+template <class E, class Epi, int V>
+fx_status launch_tile_async(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C,
+                            const Epi& epi, RedArgs red) {
+  using Cf = TileAsyncCfg<E, V>;
+  auto kern = k_tile_async<E, Epi, V, Cf::TR, Cf::TC, Cf::NT, Cf::NBUF>;
+  FX_TRY(allow_smem(kern, Cf::SMEM));
+  const int64_t ntiles = ((R + Cf::TR - 1) / Cf::TR) * ((C + Cf::TC - 1) / Cf::TC);
+  const int sms = device_sms() > 0 ? device_sms() : 1;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cf::NT, Cf::SMEM) != cudaSuccess || occ < 1) occ = 1;
+  const int bps = r.tune.bps > 0 ? (r.tune.bps < occ ? r.tune.bps : occ) : occ;
+  int64_t grid = int64_t(sms) * bps;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  if constexpr (Epi::reduces) FX_TRY(red_space(r, int(grid), red));
+  kern<<<unsigned(grid), Cf::NT, Cf::SMEM, r.st>>>(e, sl, R, C, epi, red);
+  return after_launch(r, "k_tile_async");
+}
+
+// Tiles of a tree with transposed leaves: the cp.async pipeline when the
+// launch shape asks for it and every plain leaf and the output are
+// vector-aligned, else the register kernel.
+template <class E, class EpiV, class Epi1, int V>
+fx_status launch_tiles(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C, bool vec,
+                       const EpiV& ev, const Epi1& e1, RedArgs red) {
+  using LL = leaves_t<E>;
+  if constexpr (count_mt<LL>() > 0 && V > 1 && TileAsyncCfg<E, V>::SMEM <= 200 * 1024) {
+    if (r.tune.pipe == 1 && vec && mt_pairs_ok<LL>(r.b))
+      return launch_tile_async<E, EpiV, V>(r, e, sl, R, C, ev, red);
+  }
+  if (vec) return launch_tile<E, EpiV, V>(r, e, sl, R, C, ev, red);
+  return launch_tile<E, Epi1, 1>(r, e, sl, R, C, e1, red);
+}
+
 // ---------------------------------------------------------------- element-wise
 
 template <class T, class E> fx_status run_elementwise(const Run& r, const E& e) {
@@ -297,9 +355,9 @@ template <class T, class E> fx_status run_elementwise(const Run& r, const E& e) 
       return launch_flat<E, EpiStore<T, 1>, 1>(r, e, sl, R * C, EpiStore<T, 1>{z, R}, {}, R);
     }
   }
-  if (leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0)
-    return launch_tile<E, EpiStore<T, V>, V>(r, e, sl, R, C, EpiStore<T, V>{z, zb.ld}, {});
-  return launch_tile<E, EpiStore<T, 1>, 1>(r, e, sl, R, C, EpiStore<T, 1>{z, zb.ld}, {});
+  const bool vec = leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0;
+  return launch_tiles<E, EpiStore<T, V>, EpiStore<T, 1>, V>(
+      r, e, sl, R, C, vec, EpiStore<T, V>{z, zb.ld}, EpiStore<T, 1>{z, zb.ld}, {});
 }
 
 // Element-wise tree plus its accu (outputs Z and s).
@@ -326,9 +384,9 @@ template <class T, class E> fx_status run_multi(const Run& r, const E& e) {
                                                   R);
     }
   }
-  if (leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0)
-    return launch_tile<E, EpiStoreSum<T, V>, V>(r, e, sl, R, C, EpiStoreSum<T, V>{z, zb.ld}, red);
-  return launch_tile<E, EpiStoreSum<T, 1>, 1>(r, e, sl, R, C, EpiStoreSum<T, 1>{z, zb.ld}, red);
+  const bool vec = leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0;
+  return launch_tiles<E, EpiStoreSum<T, V>, EpiStoreSum<T, 1>, V>(
+      r, e, sl, R, C, vec, EpiStoreSum<T, V>{z, zb.ld}, EpiStoreSum<T, 1>{z, zb.ld}, red);
 }
 
 // ---------------------------------------------------------------- A5: accu, norm
@@ -355,9 +413,8 @@ template <class T, class Root> fx_status run_full_reduce(const Run& r, const Roo
       return launch_flat<E, EpiSum<CT, 1, SQ>, 1>(r, e, sl, R * C, EpiSum<CT, 1, SQ>{R}, red, R);
     }
   }
-  if (leaves_vec<LL, V>(r.b))
-    return launch_tile<E, EpiSum<CT, V, SQ>, V>(r, e, sl, R, C, EpiSum<CT, V, SQ>{0}, red);
-  return launch_tile<E, EpiSum<CT, 1, SQ>, 1>(r, e, sl, R, C, EpiSum<CT, 1, SQ>{0}, red);
+  return launch_tiles<E, EpiSum<CT, V, SQ>, EpiSum<CT, 1, SQ>, V>(
+      r, e, sl, R, C, leaves_vec<LL, V>(r.b), EpiSum<CT, V, SQ>{0}, EpiSum<CT, 1, SQ>{0}, red);
 }
 
 // ---------------------------------------------------------------- A6: sum / max along a dim
@@ -406,7 +463,7 @@ fx_status launch_row(const Run& r, const E& e, const Slots& sl, int64_t R, int64
     return FX_OK;
   };
   if constexpr (V > 1) {
-   if (r.tune.bulk && leaves_bulk<LL>(r.b, R)) {
+   if (r.tune.pipe == 1 && leaves_bulk<LL>(r.b, R)) {
     constexpr int CPS = 2;
     auto kern = k_row_bulk<E, ISMAX, V, NT, NS, CPS>;
     constexpr int smem = NS * CPS * stage_bytes<LL, NT * V>() + int(sizeof(Ring<NS>));

@@ -26,7 +26,9 @@ struct Tune {
   int unroll = 4;
   int bps = 0;
   bool tuned = false;
-  bool bulk = false;  // row reductions: bulk-copy pipeline instead of register loads
+  // 1: copy-pipeline kernels where a tree has them (transposed tiles staged
+  // by cp.async, row reductions fed by bulk copies); 0: register loads
+  int pipe = 0;
 };
 
 // Device workspace owned by one fx_expr: reduction partials, tickets,
@@ -109,7 +111,8 @@ std::string device_name();
 size_t storage_bytes(fx_dtype d);
 size_t reduce_bytes(fx_dtype d);
 
-// Tuning cache: key -> "block,unroll,bps"
+// Tuning cache: key -> "block,unroll,bps,pipeline"
+bool launch_shape_ok(int block, int unroll, int bps, int pipe);
 bool tune_cache_get(const std::string& key, Tune& t);
 void tune_cache_put(const std::string& key, const Tune& t);
 

@@ -114,7 +114,7 @@ static std::string cache_path() {
   return v && *v ? v : "fx_tune.json";
 }
 
-// The file is a flat JSON object {"key": "block,unroll,bps", ...}.
+// The file is a flat JSON object {"key": "block,unroll,bps,pipeline", ...}.
 static std::map<std::string, std::string> read_cache() {
   std::map<std::string, std::string> m;
   std::ifstream f(cache_path());
@@ -139,17 +139,21 @@ static std::map<std::string, std::string> read_cache() {
 
 static std::mutex g_cache_mu;
 
+bool launch_shape_ok(int block, int unroll, int bps, int pipe) {
+  const bool b = block >= 64 && block <= 512 && block % 32 == 0;
+  const bool u = unroll == 2 || unroll == 4 || unroll == 8;
+  return b && u && bps >= 0 && bps <= 32 && (pipe == 0 || pipe == 1);
+}
+
 bool tune_cache_get(const std::string& key, Tune& t) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   auto m = read_cache();
   auto it = m.find(key);
   if (it == m.end()) return false;
-  int b = 0, u = 0, s = 0;
-  if (sscanf(it->second.c_str(), "%d,%d,%d", &b, &u, &s) != 3) return false;
-  t.block = b;
-  t.unroll = u;
-  t.bps = s;
-  t.tuned = true;
+  int b = 0, u = 0, s = 0, p = 0;
+  if (sscanf(it->second.c_str(), "%d,%d,%d,%d", &b, &u, &s, &p) < 3) return false;
+  if (!launch_shape_ok(b, u, s, p)) return false;
+  t = Tune{b, u, s, true, p};
   return true;
 }
 
@@ -157,7 +161,7 @@ void tune_cache_put(const std::string& key, const Tune& t) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   auto m = read_cache();
   char v[64];
-  snprintf(v, sizeof v, "%d,%d,%d", t.block, t.unroll, t.bps);
+  snprintf(v, sizeof v, "%d,%d,%d,%d", t.block, t.unroll, t.bps, t.pipe);
   m[key] = v;
   std::ofstream f(cache_path());
   f << "{\n";
@@ -352,11 +356,22 @@ fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream) {
   return x->e->tune(x, int(mode), static_cast<cudaStream_t>(stream));
 }
 
-fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* bps) {
+fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* bps,
+                               int* pipeline) {
   if (!x) return fail(FX_E_ARG, "null expression");
   if (block) *block = x->tune.block;
   if (unroll) *unroll = x->tune.unroll;
   if (bps) *bps = x->tune.bps;
+  if (pipeline) *pipeline = x->tune.pipe;
+  return FX_OK;
+}
+
+fx_status fx_expr_set_launch_shape(fx_expr* x, int block, int unroll, int bps, int pipeline) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  if (!launch_shape_ok(block, unroll, bps, pipeline))
+    return fail(FX_E_ARG, "bad launch shape (block %d, unroll %d, blocks/SM %d, pipeline %d)", block,
+                unroll, bps, pipeline);
+  x->tune = Tune{block, unroll, bps, true, pipeline};
   return FX_OK;
 }
 

@@ -86,6 +86,46 @@ def test_reductions_bitwise_repeatable(fx, name):
             assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
 
 
+# Launch shapes: both kernel variants (register loads; copy pipeline, which
+# trees with transposed leaves and row reductions have), small and large
+# blocks, shallow and deep unrolling, capped residency. Shapes span several
+# tiles, split columns and ragged tails.
+SHAPES = [(256, 4, 0, 1), (128, 2, 2, 1), (512, 8, 0, 0), (64, 2, 1, 0), (256, 8, 4, 1)]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
+@pytest.mark.parametrize("name", NAMES)
+def test_launch_shapes(fx, name, storage):
+    for i, shape in enumerate(SHAPES):
+        for R, C in [(257, 129), (1000, 700), (64, 64)]:
+            env = env_for(name, storage, R, C, seed=20 + i)
+            got = run(fx, name, storage, env, R, C, shape=shape)
+            check(name, storage, got, oracle_outputs(name, env), f" at {R}x{C} shape {shape}")
+
+
+@pytest.mark.parametrize("name", ["schur_exp_trans", "schur_trans_accu", "absdiff_rowmax"])
+def test_pipeline_variant_matches_register_variant(fx, name):
+    """Both variants reduce in the same order, so their outputs agree bit for
+    bit (element-wise outputs and row maxima)."""
+    R, C = 1500, 900
+    env = env_for(name, "f32", R, C, seed=31)
+    a = run(fx, name, "f32", env, R, C, shape=(256, 4, 0, 0))
+    b = run(fx, name, "f32", env, R, C, shape=(256, 4, 0, 1))
+    assert np.array_equal(a["Z" if "Z" in a else "v"], b["Z" if "Z" in b else "v"])
+
+
+def test_launch_shape_rejects_bad_values(fx):
+    h = fx.fx_expr_create("schur_exp_trans", 0)
+    try:
+        before = fx.fx_expr_launch_shape(h)
+        for bad in [(48, 4, 0, 0), (256, 3, 0, 0), (256, 4, -1, 0), (256, 4, 0, 2), (1024, 4, 0, 0)]:
+            with pytest.raises(fx.FxError):
+                fx.fx_expr_set_launch_shape(h, *bad)
+            assert fx.fx_expr_launch_shape(h) == before
+    finally:
+        fx.fx_expr_destroy(h)
+
+
 def test_one_launch_per_fused_tree(fx):
     for name in NAMES:
         env = env_for(name, "f32", 300, 200)
