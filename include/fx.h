@@ -182,20 +182,22 @@ fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream);
 
 /* Launch shape currently chosen (for reports): threads per block, vectors
  * per thread per step, blocks per SM (0: as many as fit), and the kernel
- * variant (0: register loads; 1: copy pipeline, see
- * fx_expr_set_launch_shape). Null pointers are skipped. */
+ * variant (see fx_expr_set_launch_shape). Null pointers are skipped. */
 fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* blocks_per_sm,
                                int* pipeline);
 
 /* Fixes the launch shape (what FX_TUNE_SEARCH would choose) until the next
  * fx_tune call. block: threads per block of the streaming kernels, a
  * multiple of 32 in [64, 512]; unroll: 2, 4 or 8 vectors per thread per
- * step; blocks_per_sm: 0 (as many as fit) to 32; pipeline: 0 for the
- * register-load kernels, 1 for the copy-pipeline variants where a tree has
- * one (trees with transposed leaves stage their tiles through a cp.async
- * ring; sum/max along dim 1 is fed by bulk copies), used only when the
- * operands meet that variant's alignment rules. Results are the same
- * within each kernel's rounding rules; the choice changes speed only.
+ * step; blocks_per_sm: 0 (as many as fit) to 32; pipeline: the kernel
+ * variant where a tree has several. Trees with transposed leaves: 0 moves
+ * tiles with tensor-map (TMA) copies, 1 stages them through a cp.async
+ * ring, 2 stages them through registers. Sum/max along dim 1: 1 feeds the
+ * rows by bulk copies, 0 and 2 load them into registers. A variant whose
+ * alignment rules the operands miss (TMA: 16-byte aligned bases and
+ * leading dimensions of a multiple of 16 bytes) falls back to the register
+ * kernel. Results agree within each kernel's rounding rules; the choice
+ * changes speed only.
  * FX_E_ARG for a value out of range (the shape is then unchanged). */
 fx_status fx_expr_set_launch_shape(fx_expr* x, int block, int unroll, int blocks_per_sm,
                                    int pipeline);

@@ -171,6 +171,7 @@ FX_D void load_rc(Pack<LL, V, CT>& p, const Slots& sl, int64_t r, int64_t c, int
 template <class T, int V> struct EpiStore {
   T* z;
   int64_t ldz;
+  static constexpr bool stores = true;
   static constexpr bool reduces = false;
   static constexpr bool sqrt_result = false;
   struct State {
@@ -193,6 +194,7 @@ template <class T, int V> struct EpiStore {
 // Fused sum of the elements (SQ: of their squares, for the 2-norm).
 template <class CTy, int V, bool SQ> struct EpiSum {
   int64_t ldz;
+  static constexpr bool stores = false;
   static constexpr bool reduces = true;
   static constexpr bool sqrt_result = SQ;
   using State = ThreadSum<CTy>;
@@ -207,6 +209,7 @@ template <class CTy, int V, bool SQ> struct EpiSum {
 template <class T, int V> struct EpiStoreSum {
   T* z;
   int64_t ldz;
+  static constexpr bool stores = true;
   static constexpr bool reduces = true;
   static constexpr bool sqrt_result = false;
   using State = ThreadSum<compute_t<T>>;

@@ -6,7 +6,8 @@
 #include <cmath>
 #include <string>
 
-#include "async.cuh"
+
+#include "tmatile.cuh"
 #include "runtime.hpp"
 
 namespace fx {
@@ -54,13 +55,15 @@ template <class LL, int I = 0> bool leaves_bulk(const Binding* b, int64_t R) {
 }
 
 // Dynamic shared memory above 48 KB must be allowed once per kernel.
+// Sets a kernel's dynamic shared-memory limit before each launch that
+// needs more than the default 48 KB. Not cached: a template kernel
+// instantiated in several translation units is one host symbol over
+// several device functions, so a per-instantiation "already set" flag can
+// skip the function that is about to run.
 template <class K> fx_status allow_smem(K kern, int bytes) {
-  static bool done = false;  // one flag per kernel instantiation
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-    done = true;
-  }
+  if (bytes <= 48 * 1024) return FX_OK;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
   return FX_OK;
 }
 
@@ -320,13 +323,79 @@ fx_status launch_tile_async(const Run& r, const E& e, const Slots& sl, int64_t R
   return after_launch(r, "k_tile_async");
 }
 
-// Tiles of a tree with transposed leaves: the cp.async pipeline when the
-// launch shape asks for it and every plain leaf and the output are
-// vector-aligned, else the register kernel.
-template <class E, class EpiV, class Epi1, int V>
+// k_tile_tma: one CTA per SM (two with blocks_per_sm >= 2), as many
+// stages as fit next to the two output tiles. *used is false when the
+// operands are not TMA-addressable or fewer than two stages fit.
+template <class T, class E, class Epi>
+fx_status launch_tile_tma(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C,
+                          const Epi& epi, RedArgs red, bool* used) {
+  using LL = leaves_t<E>;
+  using G = TmaGeom<T>;
+  *used = false;
+  if constexpr (!tma_uniform<LL, T>()) {
+    return FX_OK;
+  } else {
+    constexpr int NTC = 256;
+    constexpr int SB = count_tma<LL>() * G::LEAF;
+    TileMaps tm;
+    if (!encode_leaf_maps<LL, T>(tm, r.b)) return FX_OK;
+    if constexpr (Epi::stores) {
+      if (!encode_tile_map<T>(&tm.m[r.n_in], epi.z, R, C, epi.ldz)) return FX_OK;
+    }
+    const int fixed = (Epi::stores ? 2 * G::LEAF : 0) + int(sizeof(Ring<kTmaMaxStages>)) + 1024;
+    // 227 KB per block, less 2 KB for the combine's static shared memory
+    const int budget = (r.tune.bps >= 2 ? 113 * 1024 : 227 * 1024) - 2048;
+    int ns = (budget - fixed) / SB;
+    if (ns > kTmaMaxStages) ns = kTmaMaxStages;
+    if (ns < 2) return FX_OK;
+    const int smem = ns * SB + fixed;
+    auto kern = k_tile_tma<E, Epi, T, NTC>;
+    FX_TRY(allow_smem(kern, smem));
+    unsigned int* err = nullptr;
+    FX_TRY(err_word(r, &err));
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTC + 32, smem) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    const int sms = device_sms() > 0 ? device_sms() : 1;
+    const int64_t ntiles = ((R + G::TT - 1) / G::TT) * ((C + G::TT - 1) / G::TT);
+    int64_t grid = int64_t(sms) * occ;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    if constexpr (Epi::reduces) FX_TRY(red_space(r, int(grid), red));
+    *used = true;
+    kern<<<unsigned(grid), NTC + 32, smem, r.st>>>(e, sl, R, C, epi, red, tm, r.n_in, ns, err);
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, kern);
+      cudaGetLastError();
+      return fail(FX_E_CUDA,
+                  "k_tile_tma: %s (grid %lld, %d stages, %d + %d bytes of shared memory, limit %d, "
+                  "%d registers)",
+                  cudaGetErrorString(le), (long long)grid, ns, smem, int(fa.sharedSizeBytes),
+                  fa.maxDynamicSharedSizeBytes, fa.numRegs);
+    }
+    return after_launch(r, "k_tile_tma");
+  }
+}
+
+// Tiles of a tree with transposed leaves. Launch-shape pipeline 0: the
+// TMA kernel when the operands allow it; 1: the cp.async pipeline when
+// every plain leaf and the output are vector-aligned; otherwise, and for
+// pipeline 2, the register-staged kernel.
+template <class T, class E, class EpiV, class Epi1, int V>
 fx_status launch_tiles(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C, bool vec,
                        const EpiV& ev, const Epi1& e1, RedArgs red) {
   using LL = leaves_t<E>;
+  if constexpr (count_mt<LL>() > 0) {
+    if (r.tune.pipe == 0) {
+      bool used = false;
+      const fx_status s = launch_tile_tma<T>(r, e, sl, R, C, ev, red, &used);
+      if (s != FX_OK || used) return s;
+    }
+  }
   if constexpr (count_mt<LL>() > 0 && V > 1 && TileAsyncCfg<E, V>::SMEM <= 200 * 1024) {
     if (r.tune.pipe == 1 && vec && mt_pairs_ok<LL>(r.b))
       return launch_tile_async<E, EpiV, V>(r, e, sl, R, C, ev, red);
@@ -356,7 +425,7 @@ template <class T, class E> fx_status run_elementwise(const Run& r, const E& e) 
     }
   }
   const bool vec = leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0;
-  return launch_tiles<E, EpiStore<T, V>, EpiStore<T, 1>, V>(
+  return launch_tiles<T, E, EpiStore<T, V>, EpiStore<T, 1>, V>(
       r, e, sl, R, C, vec, EpiStore<T, V>{z, zb.ld}, EpiStore<T, 1>{z, zb.ld}, {});
 }
 
@@ -385,7 +454,7 @@ template <class T, class E> fx_status run_multi(const Run& r, const E& e) {
     }
   }
   const bool vec = leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0;
-  return launch_tiles<E, EpiStoreSum<T, V>, EpiStoreSum<T, 1>, V>(
+  return launch_tiles<T, E, EpiStoreSum<T, V>, EpiStoreSum<T, 1>, V>(
       r, e, sl, R, C, vec, EpiStoreSum<T, V>{z, zb.ld}, EpiStoreSum<T, 1>{z, zb.ld}, red);
 }
 
@@ -413,7 +482,7 @@ template <class T, class Root> fx_status run_full_reduce(const Run& r, const Roo
       return launch_flat<E, EpiSum<CT, 1, SQ>, 1>(r, e, sl, R * C, EpiSum<CT, 1, SQ>{R}, red, R);
     }
   }
-  return launch_tiles<E, EpiSum<CT, V, SQ>, EpiSum<CT, 1, SQ>, V>(
+  return launch_tiles<T, E, EpiSum<CT, V, SQ>, EpiSum<CT, 1, SQ>, V>(
       r, e, sl, R, C, leaves_vec<LL, V>(r.b), EpiSum<CT, V, SQ>{0}, EpiSum<CT, 1, SQ>{0}, red);
 }
 

@@ -26,8 +26,9 @@ struct Tune {
   int unroll = 4;
   int bps = 0;
   bool tuned = false;
-  // 1: copy-pipeline kernels where a tree has them (transposed tiles staged
-  // by cp.async, row reductions fed by bulk copies); 0: register loads
+  // kernel variant where a tree has several: transposed tiles by TMA (0),
+  // cp.async (1) or registers (2); rows of dim-1 reductions by bulk copies
+  // (1) or registers (0, 2)
   int pipe = 0;
 };
 

@@ -142,7 +142,7 @@ static std::mutex g_cache_mu;
 bool launch_shape_ok(int block, int unroll, int bps, int pipe) {
   const bool b = block >= 64 && block <= 512 && block % 32 == 0;
   const bool u = unroll == 2 || unroll == 4 || unroll == 8;
-  return b && u && bps >= 0 && bps <= 32 && (pipe == 0 || pipe == 1);
+  return b && u && bps >= 0 && bps <= 32 && pipe >= 0 && pipe <= 2;
 }
 
 bool tune_cache_get(const std::string& key, Tune& t) {

@@ -86,11 +86,11 @@ def test_reductions_bitwise_repeatable(fx, name):
             assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
 
 
-# Launch shapes: both kernel variants (register loads; copy pipeline, which
-# trees with transposed leaves and row reductions have), small and large
+# Launch shapes: every kernel variant (transposed tiles by TMA, cp.async or
+# registers; dim-1 rows by bulk copies or registers), small and large
 # blocks, shallow and deep unrolling, capped residency. Shapes span several
 # tiles, split columns and ragged tails.
-SHAPES = [(256, 4, 0, 1), (128, 2, 2, 1), (512, 8, 0, 0), (64, 2, 1, 0), (256, 8, 4, 1)]
+SHAPES = [(256, 4, 0, 1), (128, 2, 2, 1), (512, 8, 0, 0), (64, 2, 1, 2), (256, 8, 4, 2)]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
@@ -104,21 +104,49 @@ def test_launch_shapes(fx, name, storage):
 
 
 @pytest.mark.parametrize("name", ["schur_exp_trans", "schur_trans_accu", "absdiff_rowmax"])
-def test_pipeline_variant_matches_register_variant(fx, name):
-    """Both variants reduce in the same order, so their outputs agree bit for
-    bit (element-wise outputs and row maxima)."""
+def test_kernel_variants_agree_bitwise(fx, name):
+    """Every variant evaluates an element with the same operations, so the
+    element-wise outputs and the row maxima agree bit for bit."""
     R, C = 1500, 900
     env = env_for(name, "f32", R, C, seed=31)
-    a = run(fx, name, "f32", env, R, C, shape=(256, 4, 0, 0))
-    b = run(fx, name, "f32", env, R, C, shape=(256, 4, 0, 1))
-    assert np.array_equal(a["Z" if "Z" in a else "v"], b["Z" if "Z" in b else "v"])
+    outs = [run(fx, name, "f32", env, R, C, shape=(256, 4, 0, p)) for p in (0, 1, 2)]
+    key = "Z" if "Z" in outs[0] else "v"
+    for o in outs[1:]:
+        assert np.array_equal(outs[0][key], o[key])
+
+
+# Shapes whose leading dimensions TMA can address (multiples of 16 bytes):
+# ragged last tiles, last tiles whose second box starts outside the matrix
+# (972 rows in FP32: boxes at 960 and 992; 970 rows in FP64: 960 and 976;
+# 712 columns: 704 and 736), and a single full tile.
+TMA_SHAPES = {"f32": [(1000, 700), (972, 712), (64, 64)], "bf16": [(1000, 712), (968, 136)],
+              "f16": [(1000, 712)], "f64": [(1000, 702), (970, 98)]}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
+@pytest.mark.parametrize("name", ["schur_exp_trans", "schur_trans_accu"])
+def test_tma_tiles(fx, name, storage):
+    for k, (R, C) in enumerate(TMA_SHAPES[storage]):
+        env = env_for(name, storage, R, C, seed=40 + k)
+        ref = oracle_outputs(name, env)
+        for pipe in (0, 1, 2):
+            got = run(fx, name, storage, env, R, C, shape=(256, 4, 0, pipe))
+            check(name, storage, got, ref, f" at {R}x{C} pipeline {pipe}")
+        got = run(fx, name, storage, env, R, C, shape=(256, 4, 2, 0))
+        check(name, storage, got, ref, f" at {R}x{C} two blocks per SM")
+    # padded leading dimensions, still 16-byte multiples, on leaves and output
+    R, C = 520, 264
+    lds = {s: rows + 8 for s, rows, _ in specs_for(name, R, C)}
+    env = env_for(name, storage, R, C, seed=49, lds=lds)
+    got = run(fx, name, storage, env, R, C, ldz=R + 8, shape=(256, 4, 0, 0))
+    check(name, storage, got, oracle_outputs(name, env), " (padded leading dimensions)")
 
 
 def test_launch_shape_rejects_bad_values(fx):
     h = fx.fx_expr_create("schur_exp_trans", 0)
     try:
         before = fx.fx_expr_launch_shape(h)
-        for bad in [(48, 4, 0, 0), (256, 3, 0, 0), (256, 4, -1, 0), (256, 4, 0, 2), (1024, 4, 0, 0)]:
+        for bad in [(48, 4, 0, 0), (256, 3, 0, 0), (256, 4, -1, 0), (256, 4, 0, 3), (1024, 4, 0, 0)]:
             with pytest.raises(fx.FxError):
                 fx.fx_expr_set_launch_shape(h, *bad)
             assert fx.fx_expr_launch_shape(h) == before
