@@ -343,10 +343,16 @@ fx_status launch_tile_tma(const Run& r, const E& e, const Slots& sl, int64_t R, 
       if (!encode_tile_map<T>(&tm.m[r.n_in], epi.z, R, C, epi.ldz)) return FX_OK;
     }
     const int fixed = (Epi::stores ? 2 * G::LEAF : 0) + int(sizeof(Ring<kTmaMaxStages>)) + 1024;
-    // 227 KB per block, less 2 KB for the combine's static shared memory
-    const int budget = (r.tune.bps >= 2 ? 113 * 1024 : 227 * 1024) - 2048;
-    int ns = (budget - fixed) / SB;
-    if (ns > kTmaMaxStages) ns = kTmaMaxStages;
+    // Two CTAs per SM when two stages fit in half the shared memory (their
+    // 16 consumer warps keep up with HBM on BF16 trees, where 8 do not),
+    // else one; blocks_per_sm 1 or 2 forces the choice. 227 KB per SM,
+    // less 2 KB per CTA for the combine's static shared memory.
+    auto stages = [&](int per_sm) {
+      const int n = ((227 * 1024) / per_sm - 2048 - fixed) / SB;
+      return n > kTmaMaxStages ? kTmaMaxStages : n;
+    };
+    int ns = r.tune.bps == 1 ? 0 : stages(2);
+    if (ns < 2 && r.tune.bps < 2) ns = stages(1);
     if (ns < 2) return FX_OK;
     const int smem = ns * SB + fixed;
     auto kern = k_tile_tma<E, Epi, T, NTC>;
