@@ -189,15 +189,19 @@ fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* b
 /* Fixes the launch shape (what FX_TUNE_SEARCH would choose) until the next
  * fx_tune call. block: threads per block of the streaming kernels, a
  * multiple of 32 in [64, 512]; unroll: 2, 4 or 8 vectors per thread per
- * step; blocks_per_sm: 0 (as many as fit) to 32; pipeline: the kernel
- * variant where a tree has several. Trees with transposed leaves: 0 moves
- * tiles with tensor-map (TMA) copies, 1 stages them through a cp.async
- * ring, 2 stages them through registers. Sum/max along dim 1: 1 feeds the
- * rows by bulk copies, 0 and 2 load them into registers. A variant whose
- * alignment rules the operands miss (TMA: 16-byte aligned bases and
- * leading dimensions of a multiple of 16 bytes) falls back to the register
- * kernel. Results agree within each kernel's rounding rules; the choice
- * changes speed only.
+ * step; blocks_per_sm: 0 (as many as fit) to 32 (the shared-memory
+ * pipelines take 1 or 2); pipeline: the kernel variant.
+ *   0: the library's choice per tree: tensor-map (TMA) tiles for trees
+ *      with transposed leaves, bulk-copy chunks for dense trees of five or
+ *      more leaves, register loads otherwise;
+ *   1: copy pipelines wherever a tree has one: cp.async tiles for
+ *      transposed leaves, bulk-copy chunks for dense trees, bulk-copy row
+ *      segments for sum/max along dim 1;
+ *   2: register loads everywhere.
+ * A variant whose alignment rules the operands miss (TMA and bulk copies:
+ * 16-byte aligned bases; TMA also leading dimensions of a multiple of 16
+ * bytes) falls back to register loads. Results agree within each kernel's
+ * rounding rules; the choice changes speed only.
  * FX_E_ARG for a value out of range (the shape is then unchanged). */
 fx_status fx_expr_set_launch_shape(fx_expr* x, int block, int unroll, int blocks_per_sm,
                                    int pipeline);

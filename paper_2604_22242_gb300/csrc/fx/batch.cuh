@@ -6,8 +6,8 @@
 // walks the list with a static stride and runs the same tile body as the
 // single-matrix tiled kernel (transposed leaves staged through shared
 // memory). A tree with an accu output writes one compensated partial per
-// tile; a second launch sums each matrix's partials in tile order in FP64
-// (one warp per matrix). The list, the descriptors and both launches are
+// warp of each tile; a second launch sums each matrix's partials in order
+// in FP64 (one warp per matrix). The list, the descriptors and both launches are
 // cached per item array; with use_graph the launches are captured once in a
 // CUDA graph and replayed.
 #pragma once
@@ -37,16 +37,15 @@ struct BatchItem {
 //
 // k_batch_async: each block walks its work items (static stride) with an
 // NBUF-deep pipeline. For the item NBUF-1 ahead, every thread issues
-// asynchronous global->shared copies (cp.async, 4 bytes each, consecutive
-// threads on consecutive elements of a column, so every copy instruction
-// of a warp is coalesced) of the tile's plain leaves (stored column-major,
-// TR rows per column) and transposed leaves (stored as D's columns, TC+1
-// elements per row, so reads in output order avoid bank conflicts); then
-// it waits for the item in front, evaluates the tile from shared memory
-// one element per thread-step, stores Z and reduces. Copies cost shared
-// memory instead of registers, and the item's descriptor is read one
-// item ahead, so the dependent global loads leave the critical path.
-
+// asynchronous global->shared copies (cp.async) of the tile's plain leaves
+// (stored column-major, TR rows per column; 16-byte chunks where the source
+// allows, single elements elsewhere) and transposed leaves (stored as D's
+// columns, TC+1 elements per row, so reads in output order avoid bank
+// conflicts); then it waits for the item in front, evaluates the tile from
+// shared memory V rows of a column per thread-step, stores Z (16-byte
+// stores where aligned) and reduces. Copies cost shared memory instead of
+// registers, and the item's descriptor is read one item ahead, so the
+// dependent global loads leave the critical path.
 
 // Per-item fields the evaluation needs, kept per buffer in shared memory.
 struct TileDesc {
@@ -109,10 +108,14 @@ FX_D IssueDesc<NIN> fetch_item(const BatchMat* mats, const BatchItem* items, int
   return d;
 }
 
-// Thread t copies rows (t % TR) [+W-blocks] of columns t / TR, t / TR + NT/TR, ...
-// of each plain leaf, and elements (t % TC) of D's columns t / TC, ... of
-// each transposed leaf; interior tiles skip every bounds test. Offsets are
-// 32-bit: a batch matrix holds fewer than 2^31 elements.
+// Copies of one item's tile. Plain leaves: thread t takes the W-element
+// chunk (t % (TR/W)) of columns t / (TR/W), + NT/(TR/W), ... (W = 16 bytes
+// of elements) and moves it with one 16-byte copy when its source is
+// 16-byte aligned and wholly inside the matrix, else element by element
+// (matrices of any shape and leading dimension). Transposed leaves: thread
+// t takes element t % TC of D's columns t / TC, ...; stored as TR rows of
+// TC + 1 elements. Offsets are 32-bit: a batch matrix holds fewer than
+// 2^31 elements.
 template <class LL, int TR, int TC, int NT, int NIN, int I = 0>
 FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d, bool full) {
   if constexpr (I < tl_size<LL>::value) {
@@ -123,23 +126,23 @@ FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d, bool full) {
     const int rr = int(d.R - d.r0), cc = int(d.C - d.c0);  // rows / cols left in the matrix
     if constexpr (L::mode == MN) {
       const T* src = static_cast<const T*>(d.p[L::slot]) + d.r0 + d.c0 * int64_t(ld);
-      constexpr int W = 16 / int(sizeof(T));  // elements per 16-byte copy
-      if (W > 1 && sizeof(T) >= 4 && d.vec && full) {
-        static_assert((TR / W) * TC % NT == 0 && NT % (TR / W) == 0, "vector copy shape");
-        const int r = (threadIdx.x % (TR / W)) * W;
+      constexpr int W = 16 / int(sizeof(T));
+      constexpr int CPC = TR / W;  // chunks per column
+      static_assert(NT % CPC == 0 && TC % (NT / CPC) == 0, "chunk copy shape");
+      const int r = (threadIdx.x % CPC) * W;
 #pragma unroll
-        for (int c = threadIdx.x / (TR / W); c < TC; c += NT / (TR / W))
-          cpa::copy16(dst + c * TR + r, src + r + c * ld);
-      } else {
-        static_assert(NT % TR == 0, "scalar copy shape");
-        const int r = threadIdx.x % TR;
-        if (full) {
+      for (int c = threadIdx.x / CPC; c < TC; c += NT / CPC) {
+        const T* s = src + r + c * ld;
+        T* t = dst + c * TR + r;
+        if (full || (c < cc && r + W <= rr)) {
+          if ((reinterpret_cast<uintptr_t>(s) & 15) == 0) {
+            cpa::copy16(t, s);
+          } else {
 #pragma unroll
-          for (int c = threadIdx.x / TR; c < TC; c += NT / TR)
-            cpa::copy<int(sizeof(T))>(dst + c * TR + r, src + r + c * ld);
-        } else if (r < rr) {
-          for (int c = threadIdx.x / TR; c < TC && c < cc; c += NT / TR)
-            cpa::copy<int(sizeof(T))>(dst + c * TR + r, src + r + c * ld);
+            for (int j = 0; j < W; ++j) cpa::copy<int(sizeof(T))>(t + j, s + j);
+          }
+        } else if (c < cc) {
+          for (int j = 0; j < W && r + j < rr; ++j) cpa::copy<int(sizeof(T))>(t + j, s + j);
         }
       }
     } else if constexpr (L::mode == MT) {
@@ -159,24 +162,28 @@ FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d, bool full) {
   }
 }
 
-// Element (r, c) of the tile (local indices) of every leaf into a V=1 pack.
-template <class LL, class CT, int TR, int TC, int I = 0>
-FX_D void load_tile_elem(Pack<LL, 1, CT>& p, const char* buf, const BatchMat& m, int64_t r0,
-                         int64_t c0, int r, int c) {
+// Rows r..r+V-1 of tile column c of every leaf.
+template <class LL, int V, class CT, int TR, int TC, int I = 0>
+FX_D void load_tile_vec(Pack<LL, V, CT>& p, const char* buf, const BatchMat& m, int64_t r0,
+                        int64_t c0, int r, int c, int nvalid) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
     using T = typename L::elem;
     const T* b = reinterpret_cast<const T*>(buf + abuf_offset<LL, TR, TC, I>());
+    auto& dst = pget<I>::of(p);
     if constexpr (L::mode == MN) {
-      pget<I>::of(p).v[0] = b[c * TR + r];
+      dst = *reinterpret_cast<const Raw<T, V>*>(b + c * TR + r);
     } else if constexpr (L::mode == MT) {
-      pget<I>::of(p).v[0] = to_compute<CT>(b[r * (TC + 1) + c]);
+#pragma unroll
+      for (int j = 0; j < V; ++j) dst.v[j] = to_compute<CT>(b[(r + j) * (TC + 1) + c]);
     } else if constexpr (L::mode == MBC) {
-      pget<I>::of(p).v[0] = sload(static_cast<const T*>(m.p[L::slot]) + (r0 + r));
+      const T* q = static_cast<const T*>(m.p[L::slot]) + (r0 + r);
+#pragma unroll
+      for (int j = 0; j < V; ++j) dst.v[j] = j < nvalid ? sload(q + j) : T(0.0f);
     } else {
-      pget<I>::of(p).v[0] = sload(static_cast<const T*>(m.p[L::slot]) + (c0 + c));
+      dst.v[0] = sload(static_cast<const T*>(m.p[L::slot]) + (c0 + c));
     }
-    load_tile_elem<LL, CT, TR, TC, I + 1>(p, buf, m, r0, c0, r, c);
+    load_tile_vec<LL, V, CT, TR, TC, I + 1>(p, buf, m, r0, c0, r, c, nvalid);
   }
 }
 
@@ -215,54 +222,77 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
     const int b = int(j % NBUF);
     const TileDesc d = desc[b];
     const BatchMat& m = mats[d.mat];
-    // a thread adds at most TC*TR/NT values of a tile: a plain sum; the block
-    // merge across threads and the per-matrix combine are compensated
+    // V consecutive rows of one column per step; a thread adds at most
+    // TR*TC/NT values of a tile: a plain sum, merged compensated per warp
+    constexpr int V = 16 / int(sizeof(T));
+    constexpr int RG = TR / V;  // row groups per column
+    static_assert(NT % RG == 0 && TC % (NT / RG) == 0, "consumer shape");
     CT tsum = CT(0);
     const char* buf = smem + b * AB;
-    const int r = threadIdx.x % TR;
+    const int r = (threadIdx.x % RG) * V;
     const int rr = int(d.R - d.r0), cc = int(d.C - d.c0);
+    const int nvalid = clamp_valid(rr - r, V);
     T* z = KIND != FX_KIND_FULL_REDUCE
                ? static_cast<T*>(const_cast<void*>(d.z)) + d.r0 + d.c0 * d.ldz
                : nullptr;
     const int ldz = int(d.ldz);
-    if (r < rr) {
-#pragma unroll 4
-      for (int c = threadIdx.x / TR; c < TC; c += NT / TR) {
+    if (nvalid > 0) {
+#pragma unroll
+      for (int c = threadIdx.x / RG; c < TC; c += NT / RG) {
         if (c < cc) {
-          Pack<LL, 1, CT> p;
-          load_tile_elem<LL, CT, TR, TC>(p, buf, m, d.r0, d.c0, r, c);
-          Ctx<LL, 1, CT> cx{p, 0};
-          const CT v = e.ev(cx);
-          if constexpr (KIND != FX_KIND_FULL_REDUCE) sstore(z + r + c * ldz, narrow_to<T>::from(v));
-          if constexpr (KIND != FX_KIND_ELEMENTWISE) tsum += v;
+          Pack<LL, V, CT> p;
+          load_tile_vec<LL, V, CT, TR, TC>(p, buf, m, d.r0, d.c0, r, c, nvalid);
+          CT v[V];
+          eval_lanes<V>(e, p, v);
+          if constexpr (KIND != FX_KIND_FULL_REDUCE) {
+            T* q = z + r + c * ldz;
+            if (nvalid == V && (reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+              Raw<T, V> o;
+#pragma unroll
+              for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(v[j]);
+              vstore(q, o);
+            } else {
+#pragma unroll
+              for (int j = 0; j < V; ++j)
+                if (j < nvalid) sstore(q + j, narrow_to<T>::from(v[j]));
+            }
+          }
+          if constexpr (KIND != FX_KIND_ELEMENTWISE) {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+              if (j < nvalid) tsum += v[j];
+          }
         }
       }
     }
     if constexpr (KIND != FX_KIND_ELEMENTWISE) {
+      // one partial per warp of the tile, in warp order: part[item * NW + w]
       std::conditional_t<std::is_same<CT, double>::value, PlainSum<CT>, CompSum<CT>> st;
       st.s = tsum;
       st.c = CT(0);
-      block_merge(st);
-      if (threadIdx.x == 0) part[d.item] = make_double2(double(st.s), double(st.c));
+      warp_merge(st);
+      if ((threadIdx.x & 31) == 0)
+        part[d.item * (NT / 32) + threadIdx.x / 32] = make_double2(double(st.s), double(st.c));
     }
     __syncthreads();  // buffer b is free for the item issued next
   }
   cpa::wait_pending<0>();
 }
 
-// One warp per matrix: its tiles' partials, in tile order, summed in FP64.
+// One warp per matrix: its tiles' per-warp partials (nw per tile), in
+// order, summed in FP64.
 template <class RT>
 __global__ void __launch_bounds__(256) k_batch_combine(const BatchMat* __restrict__ mats,
                                                        const int64_t nmat, const double2* part,
-                                                       const int sslot) {
+                                                       const int sslot, const int nw) {
   const int64_t i = int64_t(blockIdx.x) * 8 + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (i >= nmat) return;  // whole warps leave together
   const BatchMat& m = mats[i];
   std::conditional_t<std::is_same<RT, double>::value, CompSum<double>, PlainSum<double>> a;
   a.init();
-  for (int64_t k = lane; k < m.ntiles; k += 32) {
-    double2 q = __ldcg(part + m.first + k);
+  for (int64_t k = lane; k < int64_t(m.ntiles) * nw; k += 32) {
+    double2 q = __ldcg(part + m.first * nw + k);
     a.add(q.x);
     a.add(q.y);
   }
@@ -425,7 +455,7 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
       }
       const size_t bm = ((sizeof(BatchMat) * n) + 255) & ~size_t(255);
       const size_t bi = ((sizeof(BatchItem) * work.size()) + 255) & ~size_t(255);
-      const size_t bp = sizeof(double2) * (work.size() > 0 ? work.size() : 1);
+      const size_t bp = sizeof(double2) * (NT / 32) * (work.size() > 0 ? work.size() : 1);
       FX_TRY(c.dev.ensure(bm + bi + bp, st));
       char* base = static_cast<char*>(c.dev.p);
       c.mats = reinterpret_cast<BatchMat*>(base);
@@ -457,7 +487,7 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
         FX_TRY(after_launch(r, "k_batch_async"));
       }
       if (has_s && c.n > 0) {
-        k_batch_combine<CT><<<unsigned((c.n + 7) / 8), 256, 0, st>>>(c.mats, c.n, c.part, sslot);
+        k_batch_combine<CT><<<unsigned((c.n + 7) / 8), 256, 0, st>>>(c.mats, c.n, c.part, sslot, NT / 32);
         FX_TRY(after_launch(r, "k_batch_combine"));
       }
       return FX_OK;

@@ -195,6 +195,125 @@ FX_D void produce(char* stages, Ring<NS>& ring, const Slots& sl, int64_t r0, int
   }
 }
 
+// ---------------------------------------------------------------- flat stream
+
+// k_flat_bulk: the flat element-wise/reduction kernel for trees whose
+// leaves are all dense matrices, fed by bulk copies instead of registers
+// (trees with many leaves cannot keep enough vectors per thread in flight
+// in registers). The flat range is cut into chunks of CH elements; for each
+// of the block's chunks the producer thread copies the chunk of every leaf
+// (one cp.async.bulk per leaf) into a ring stage, and the NTC consumers
+// evaluate it from shared memory, V elements per step, storing or reducing
+// through the epilogue. Chunks cover the first n16 elements (a whole number
+// of 16-byte vectors); block 0 evaluates the few elements after them from
+// global memory.
+template <class LL, int CH, int I = 0>
+FX_D void issue_flat_chunk(char* stage, const Slots& sl, int64_t i0, uint32_t bytes_per_es,
+                           uint64_t* bar) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    const T* src = static_cast<const T*>(sl.s[L::slot].p) + i0;
+    tma::copy_g2s(stage + I * CH * int(sizeof(T)), src, bytes_per_es * uint32_t(sizeof(T)), bar);
+    issue_flat_chunk<LL, CH, I + 1>(stage, sl, i0, bytes_per_es, bar);
+  }
+}
+template <class LL, int V, class CT, int CH, int I = 0>
+FX_D void load_flat_chunk(Pack<LL, V, CT>& p, const char* stage, int k) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    using T = typename L::elem;
+    pget<I>::of(p) = *reinterpret_cast<const Raw<T, V>*>(stage + (I * CH + k) * int(sizeof(T)));
+    load_flat_chunk<LL, V, CT, CH, I + 1>(p, stage, k);
+  }
+}
+
+template <class E, class Epi, int V, int NTC, int CH>
+__global__ void __launch_bounds__(NTC + 32) k_flat_bulk(const E e, const Slots sl, const int64_t n,
+                                                         const int64_t n16, const Epi epi,
+                                                         const RedArgs red, const int ns,
+                                                         unsigned int* err) {
+  using LL = leaves_t<E>;
+  using CT = ct_of<E>;
+  using T0 = typename tl_at<LL, 0>::type::elem;
+  constexpr int SB = tl_size<LL>::value * CH * int(sizeof(T0));
+  static_assert(CH % (V * NTC) == 0, "chunk shape");
+  extern __shared__ __align__(128) char smem[];
+  Ring<8>& ring = *reinterpret_cast<Ring<8>*>(smem + ns * SB);
+  const int64_t nch = (n16 + CH - 1) / CH;
+  const int64_t G = gridDim.x;
+  const int64_t mine = nch > int64_t(blockIdx.x) ? (nch - blockIdx.x + G - 1) / G : 0;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int i = 0; i < ns; ++i) {
+      tma::mbar_init(&ring.full[i], 1);
+      tma::mbar_init(&ring.empty[i], NTC);
+    }
+    ring.abort = 0;
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+  typename Epi::State st;
+  st.init();
+  if (tid >= NTC) {
+    if (tid == NTC) {  // producer
+      bool ok = true;
+      int64_t k = 0;
+      for (; k < mine; ++k) {
+        const int s = int(k % ns);
+        if (k >= ns && !tma::wait(&ring.empty[s], uint32_t(((k - ns) / ns) & 1), err)) {
+          ok = false;
+          break;
+        }
+        const int64_t i0 = (blockIdx.x + k * G) * int64_t(CH);
+        const uint32_t cnt = uint32_t(n16 - i0 < CH ? n16 - i0 : CH);
+        tma::arrive_expect_tx(&ring.full[s], cnt * uint32_t(tl_size<LL>::value) * uint32_t(sizeof(T0)));
+        issue_flat_chunk<LL, CH>(smem + s * SB, sl, i0, cnt, &ring.full[s]);
+      }
+      if (!ok) {
+        for (int64_t j = (k > ns ? k - ns : 0); j < k; ++j)
+          tma::wait(&ring.full[j % ns], uint32_t((j / ns) & 1), nullptr);
+      }
+    }
+  } else {
+    for (int64_t k = 0; k < mine; ++k) {
+      const int s = int(k % ns);
+      if (!tma::wait(&ring.full[s], uint32_t((k / ns) & 1), err)) {
+        ring.abort = 1;
+        break;
+      }
+      const int64_t i0 = (blockIdx.x + k * G) * int64_t(CH);
+      const int cnt = int(n16 - i0 < CH ? n16 - i0 : CH);
+      const char* stage = smem + s * SB;
+#pragma unroll
+      for (int q = 0; q < CH / (V * NTC); ++q) {
+        const int kk = (tid + q * NTC) * V;
+        if (kk < cnt) {
+          Pack<LL, V, CT> p;
+          load_flat_chunk<LL, V, CT, CH>(p, stage, kk);
+          CT v[V];
+          eval_lanes<V>(e, p, v);
+          epi.put(st, i0 + kk, v, V);
+        }
+      }
+      tma::arrive(&ring.empty[s]);
+    }
+    if (blockIdx.x == 0) {  // elements after the last whole 16-byte vector
+      for (int64_t i = n16 + tid; i < n; i += NTC) {
+        Pack<LL, 1, CT> q;
+        load_flat(q, sl, i, 0, 0);
+        CT v1[1];
+        eval_lanes<1>(e, q, v1);
+        CT v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = v1[0];
+        epi.put(st, i, v, 1);
+      }
+    }
+  }
+  if constexpr (Epi::reduces) finish_full_reduce<CT, Epi::sqrt_result>(st, red);
+}
+
 // ---------------------------------------------------------------- sum/max along dim 1
 
 template <class E, bool ISMAX, int V, int NTC, int NS, int CPS>

@@ -94,14 +94,10 @@ template <class Def, class T> struct Inst {
     if constexpr (Def::batchable) return run_batch<T, Def::n_in, Def::kind>(x, root(x), n, it, st, g);
     else return fail(FX_E_UNSUPPORTED, "no batched entry");
   }
-  // Kernel variants the search times: three for trees with transposed
-  // leaves (TMA, cp.async, register tiles), two for dim reductions (bulk
-  // copies or register loads for rows), one otherwise.
+  // The search times every kernel variant (pipeline 0, 1, 2) with every
+  // block, unroll and residency choice.
   static fx_status tune(fx_expr* x, int mode, cudaStream_t st) {
-    using R0 = std::decay_t<decltype(root(x))>;
-    constexpr bool mt = count_mt<leaves_t<typename root_of<R0>::inner>>() > 0;
-    constexpr bool dim = root_of<R0>::kind == FX_KIND_DIM_REDUCE;
-    return run_tune(x, mode, st, &eval, mt ? 3 : (dim ? 2 : 1));
+    return run_tune(x, mode, st, &eval, 3);
   }
   static Entry entry() {
     return Entry{Def::name, Def::formula, dtype_of<T>::value, Def::n_in, Def::n_out, Def::n_scal,

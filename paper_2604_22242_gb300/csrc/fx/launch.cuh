@@ -247,9 +247,70 @@ template <class E> constexpr int max_unroll() {
   return nl <= 2 ? 8 : (nl <= 4 ? 4 : (nl <= 8 ? 2 : 1));
 }
 
+// k_flat_bulk for trees whose leaves are all dense matrices of one storage
+// type with 16-byte aligned bases: one CTA per SM (two when two stages fit
+// in half the shared memory), chunks of 1024 elements per leaf.
+template <class E, class Epi, int V>
+fx_status launch_flat_bulk(const Run& r, const E& e, const Slots& sl, int64_t n, const Epi& epi,
+                           RedArgs red, bool* used) {
+  using LL = leaves_t<E>;
+  *used = false;
+  if constexpr (V == 1 || count_bcast<LL>() > 0) {
+    return FX_OK;
+  } else {
+    using T0 = typename tl_at<LL, 0>::type::elem;
+    if constexpr (!tma_uniform<LL, T0>() || V * sizeof(T0) != 16) {
+      return FX_OK;
+    } else {
+      constexpr int NTC = 256, CH = 1024 * 16 / int(sizeof(T0)) / 4;
+      constexpr int SB = tl_size<LL>::value * CH * int(sizeof(T0));
+      if (!leaves_flat<LL>(r.b, 16)) return FX_OK;
+      const int fixed = int(sizeof(Ring<8>)) + 2048;
+      auto stages = [&](int per_sm) {
+        const int k = ((227 * 1024) / per_sm - fixed) / SB;
+        return k > 8 ? 8 : k;
+      };
+      int ns = r.tune.bps == 1 ? 0 : stages(2);
+      if (ns < 2 && r.tune.bps < 2) ns = stages(1);
+      if (ns < 2) return FX_OK;
+      const int smem = ns * SB + fixed;
+      auto kern = k_flat_bulk<E, Epi, V, NTC, CH>;
+      FX_TRY(allow_smem(kern, smem));
+      unsigned int* err = nullptr;
+      FX_TRY(err_word(r, &err));
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTC + 32, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+      }
+      const int64_t n16 = n - n % V;
+      const int64_t nch = (n16 + CH - 1) / CH;
+      const int sms = device_sms() > 0 ? device_sms() : 1;
+      int64_t grid = int64_t(sms) * occ;
+      if (grid > nch) grid = nch;
+      if (grid < 1) grid = 1;
+      if constexpr (Epi::reduces) FX_TRY(red_space(r, int(grid), red));
+      *used = true;
+      kern<<<unsigned(grid), NTC + 32, smem, r.st>>>(e, sl, n, n16, epi, red, ns, err);
+      return after_launch(r, "k_flat_bulk");
+    }
+  }
+}
+
+// Flat trees: the bulk-copy kernel for pipeline 1, and by default (0) for
+// five or more leaves, where the register kernel's one vector per leaf in
+// flight no longer covers HBM latency (measured on GB300: 10000^2 FP32
+// add-N, N = 5..16, 6.8-7.0 TB/s bulk against 6.5-6.7 TB/s, and 4.9 TB/s
+// for N = 16); register loads otherwise and for pipeline 2.
 template <class E, class Epi, int V>
 fx_status launch_flat(const Run& r, const E& e, const Slots& sl, int64_t n, const Epi& epi,
                       RedArgs red, int64_t flat_rows) {
+  constexpr bool many = tl_size<leaves_t<E>>::value >= 5;
+  if (r.tune.pipe == 1 || (r.tune.pipe == 0 && many)) {
+    bool used = false;
+    const fx_status s = launch_flat_bulk<E, Epi, V>(r, e, sl, n, epi, red, &used);
+    if (s != FX_OK || used) return s;
+  }
   constexpr int UM = max_unroll<E>();
   switch (r.tune.unroll) {
     case 2: return launch_flat_u<E, Epi, V, (2 < UM ? 2 : UM)>(r, e, sl, n, epi, red, flat_rows);

@@ -26,9 +26,8 @@ struct Tune {
   int unroll = 4;
   int bps = 0;
   bool tuned = false;
-  // kernel variant where a tree has several: transposed tiles by TMA (0),
-  // cp.async (1) or registers (2); rows of dim-1 reductions by bulk copies
-  // (1) or registers (0, 2)
+  // kernel variant: 0 the library's choice per tree, 1 copy pipelines
+  // (cp.async tiles, bulk-copy flat chunks and rows), 2 register loads
   int pipe = 0;
 };
 

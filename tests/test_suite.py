@@ -39,6 +39,21 @@ def test_add_n(fx, n):
         assert got["_launches"] == 1
 
 
+@pytest.mark.parametrize("n", [2, 9, 16])
+def test_add_n_bulk_copies(fx, n):
+    """The bulk-copy flat kernel (pipeline 1): several chunks per block, a
+    last chunk shorter than the rest and elements after the last whole
+    16-byte vector; one and two CTAs per SM; and the register kernel
+    (pipeline 2) on the same trees."""
+    name = f"add{n}"
+    for R, C in [(1000, 700), (333, 129), (64, 64), (5, 3)]:
+        env = synth.operands(60 + n, specs_for(name, R, C), "f32", "uniform")
+        for shape in [(256, 4, 0, 1), (256, 4, 1, 1), (256, 4, 2, 1), (256, 2, 0, 2)]:
+            got = run(fx, name, "f32", env, R, C, shape=shape)
+            check(name, got, env, f" at {R}x{C} shape {shape}")
+            assert got["_launches"] == 1
+
+
 @pytest.mark.parametrize("name", ["expr1", "expr2", "relu", "sigmoid", "swish", "gelu"])
 def test_suite_expressions(fx, name):
     shapes = SQUARE if name == "expr1" else SHAPES
