@@ -146,8 +146,15 @@ fx_status fx_eval_unfused(fx_expr* x, void* stream);
  * to device buffers as for fx_eval; host_in[k] (k < n_inputs) is copied to
  * input slot k, the tree is evaluated, and output slot j is copied to
  * host_out[j]. Host buffers are dense column-major (ld = rows) and should be
- * pinned (cudaHostAlloc) for asynchronous copies. Returns after enqueueing;
- * the caller synchronises `stream` before reading host_out. */
+ * pinned (cudaHostAlloc) for asynchronous copies. Element-wise trees with
+ * at least 32 columns whose inputs are each read in one mode run as a
+ * pipeline of up to 8 column chunks: chunk i's inputs are copied up on an
+ * internal stream while chunk i-1 is evaluated on `stream` and chunk i-2's
+ * output is copied down on a second internal stream (the object owns both
+ * streams; `stream` waits for them before the call's work is complete).
+ * Other trees copy, evaluate and copy back in order on `stream`. Returns
+ * after enqueueing; the caller synchronises `stream` before reading
+ * host_out. */
 fx_status fx_eval_host(fx_expr* x, const void* const* host_in, void* const* host_out,
                        void* stream);
 

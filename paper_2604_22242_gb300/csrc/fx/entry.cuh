@@ -78,6 +78,25 @@ inline fx_status run_tune(fx_expr* x, int mode, cudaStream_t st, EvalFn ev, int 
   return FX_OK;
 }
 
+// Access mode of every input slot of a leaf list (-1: read in two modes).
+template <class LL> struct SlotModes {
+  signed char m[FX_MAX_SLOTS];
+  constexpr SlotModes() : m{} {
+    for (int k = 0; k < FX_MAX_SLOTS; ++k) m[k] = -2;
+    fill<0>();
+    for (int k = 0; k < FX_MAX_SLOTS; ++k)
+      if (m[k] == -2) m[k] = 0;
+  }
+  template <int I> constexpr void fill() {
+    if constexpr (I < tl_size<LL>::value) {
+      using L = typename tl_at<LL, I>::type;
+      const signed char md = static_cast<signed char>(L::mode);
+      m[L::slot] = (m[L::slot] == -2 || m[L::slot] == md) ? md : static_cast<signed char>(-1);
+      fill<I + 1>();
+    }
+  }
+};
+
 template <class Def, class T> struct Inst {
   static auto root(const fx_expr* x) { return normalize(Def::template build<T>(x->scal)); }
   static fx_status eval(fx_expr* x, cudaStream_t st) {
@@ -99,11 +118,13 @@ template <class Def, class T> struct Inst {
   static fx_status tune(fx_expr* x, int mode, cudaStream_t st) {
     return run_tune(x, mode, st, &eval, 3);
   }
+  using Root = std::decay_t<decltype(normalize(Def::template build<T>(nullptr)))>;
+  static constexpr SlotModes<leaves_t<typename root_of<Root>::inner>> modes{};
   static Entry entry() {
     return Entry{Def::name, Def::formula, dtype_of<T>::value, Def::n_in, Def::n_out, Def::n_scal,
                  fx_kind(Def::kind), Def::slots, Def::defaults, &eval, &unfused,
                  Def::batchable ? &batch : nullptr, Def::differentiable ? &backward : nullptr,
-                 &tune};
+                 &tune, modes.m};
   }
 };
 

@@ -58,6 +58,9 @@ struct fx_expr {
   fx::Tune tune;
   int last_launches = 0;
   fx::BatchCache* batch = nullptr;
+  // fx_eval_host's copy streams and chunk events (created on first use)
+  cudaStream_t copy_st[2] = {nullptr, nullptr};
+  cudaEvent_t chunk_ev[2 * 8 + 1] = {};
 };
 
 namespace fx {
@@ -82,6 +85,10 @@ struct Entry {
   BatchFn eval_batch;     // may be null
   BwdFn eval_backward;    // may be null
   TuneFn tune;
+  // access mode of each input slot in the normalised tree (Mode of
+  // expr.cuh: 0 plain, 1 transposed, 2 each_col vector, 3 each_row vector);
+  // -1 for a slot read in two modes
+  const signed char* slot_modes;
 };
 
 std::vector<Entry>& registry();

@@ -212,6 +212,10 @@ fx_status fx_expr_create(const char* name, fx_dtype storage, fx_expr** out) {
 fx_status fx_expr_destroy(fx_expr* x) {
   if (!x) return FX_OK;
   free_batch_cache(x);
+  for (auto& c : x->copy_st)
+    if (c) cudaStreamDestroy(c);
+  for (auto& ev : x->chunk_ev)
+    if (ev) cudaEventDestroy(ev);
   x->ws.release();
   x->ws_tmp.release();
   x->ws_err.release();
@@ -291,11 +295,143 @@ fx_status fx_eval_unfused(fx_expr* x, void* stream) {
   return x->e->eval_unfused(x, static_cast<cudaStream_t>(stream));
 }
 
+// One host<->device copy of columns [c0, c0 + nc) of slot binding b (a
+// matrix of `rows` rows stored with leading dimension ld on the device and
+// densely on the host), or, for a transposed slot, of rows [c0, c0 + nc).
+static fx_status copy_part(const Binding& b, size_t es, int mode, void* host, int64_t c0, int64_t nc,
+                           cudaMemcpyKind kind, cudaStream_t st) {
+  char* dev = static_cast<char*>(b.p);
+  char* h = static_cast<char*>(host);
+  const size_t hpitch = size_t(b.rows) * es, dpitch = size_t(b.ld) * es;
+  if (mode == 1) {  // transposed leaf: rows [c0, c0 + nc) of every column
+    const size_t w = size_t(nc) * es;
+    void* d = dev + size_t(c0) * es;
+    void* hh = h + size_t(c0) * es;
+    if (kind == cudaMemcpyHostToDevice)
+      FX_CUDA(cudaMemcpy2DAsync(d, dpitch, hh, hpitch, w, size_t(b.cols), kind, st));
+    else
+      FX_CUDA(cudaMemcpy2DAsync(hh, hpitch, d, dpitch, w, size_t(b.cols), kind, st));
+    return FX_OK;
+  }
+  void* d = dev + size_t(c0) * dpitch;
+  void* hh = h + size_t(c0) * hpitch;
+  if (dpitch == hpitch) {
+    if (kind == cudaMemcpyHostToDevice)
+      FX_CUDA(cudaMemcpyAsync(d, hh, hpitch * size_t(nc), kind, st));
+    else
+      FX_CUDA(cudaMemcpyAsync(hh, d, hpitch * size_t(nc), kind, st));
+  } else if (kind == cudaMemcpyHostToDevice) {
+    FX_CUDA(cudaMemcpy2DAsync(d, dpitch, hh, hpitch, hpitch, size_t(nc), kind, st));
+  } else {
+    FX_CUDA(cudaMemcpy2DAsync(hh, hpitch, d, dpitch, hpitch, size_t(nc), kind, st));
+  }
+  return FX_OK;
+}
+
+// Element-wise trees whose every input is read in one mode: the columns are
+// cut into up to 8 chunks; chunk i's inputs go up on one copy stream, the
+// tree runs on chunk i on the caller's stream, and chunk i's output comes
+// down on a second copy stream, so the copies of neighbouring chunks
+// overlap the evaluation and each other.
+static fx_status eval_host_pipelined(fx_expr* x, const void* const* host_in, void* const* host_out,
+                                     cudaStream_t st, int64_t C, bool* done) {
+  const Entry& e = *x->e;
+  *done = false;
+  if (e.kind != FX_KIND_ELEMENTWISE || C < 32) return FX_OK;
+  for (int k = 0; k < e.n_in; ++k)
+    if (e.slot_modes[k] < 0) return FX_OK;
+  const size_t es = storage_bytes(e.storage);
+  for (int k = 0; k < 2; ++k)
+    if (!x->copy_st[k]) FX_CUDA(cudaStreamCreateWithFlags(&x->copy_st[k], cudaStreamNonBlocking));
+  for (auto& ev : x->chunk_ev)
+    if (!ev) FX_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaStream_t up = x->copy_st[0], down = x->copy_st[1];
+  // chunks of a multiple of 16 columns, so TMA-aligned views stay aligned
+  int64_t cw = ((C + 7) / 8 + 15) / 16 * 16;
+  const int nch = int((C + cw - 1) / cw);
+  cudaEvent_t* ev_in = x->chunk_ev;
+  cudaEvent_t* ev_out = x->chunk_ev + 8;
+  cudaEvent_t start = x->chunk_ev[16];
+  FX_CUDA(cudaEventRecord(start, st));  // earlier work on the caller's stream comes first
+  FX_CUDA(cudaStreamWaitEvent(up, start, 0));
+  FX_CUDA(cudaStreamWaitEvent(down, start, 0));
+  Binding saved[FX_MAX_SLOTS];
+  for (int k = 0; k < FX_MAX_SLOTS; ++k) saved[k] = x->b[k];
+  const int zs = e.n_in;
+  fx_status status = FX_OK;
+  x->last_launches = 0;
+  for (int i = 0; i < nch && status == FX_OK; ++i) {
+    const int64_t c0 = i * cw, nc = C - c0 < cw ? C - c0 : cw;
+    for (int k = 0; k < e.n_in && status == FX_OK; ++k) {
+      const Binding& b = saved[k];
+      const int md = e.slot_modes[k];
+      if (b.rows * b.cols == 0) continue;
+      if (md == 0 || md == 1) {
+        status = copy_part(b, es, md, const_cast<void*>(host_in[k]), c0, nc, cudaMemcpyHostToDevice, up);
+      } else if (i == 0) {  // vectors: once, whole
+        status = copy_part(b, es, 0, const_cast<void*>(host_in[k]), 0, b.cols, cudaMemcpyHostToDevice, up);
+      }
+    }
+    if (status != FX_OK) break;
+    if (cudaEventRecord(ev_in[i], up) != cudaSuccess || cudaStreamWaitEvent(st, ev_in[i], 0) != cudaSuccess) {
+      status = cuda_fail(cudaGetLastError(), "chunk events");
+      break;
+    }
+    // views of the chunk: columns [c0, c0 + nc) of plain leaves and Z, rows
+    // of transposed leaves, the matching part of each_row vectors
+    for (int k = 0; k < e.n_in; ++k) {
+      Binding& v = x->b[k];
+      v = saved[k];
+      const int md = e.slot_modes[k];
+      if (md == 0) {
+        v.p = static_cast<char*>(v.p) + size_t(c0) * size_t(v.ld) * es;
+        v.cols = nc;
+      } else if (md == 1) {
+        v.p = static_cast<char*>(v.p) + size_t(c0) * es;
+        v.rows = nc;
+      } else if (md == 3) {
+        const int64_t stride = v.rows == 1 ? v.ld : 1;
+        v.p = static_cast<char*>(v.p) + size_t(c0 * stride) * es;
+        if (v.rows == 1) v.cols = nc;
+        else v.rows = nc;
+      }
+    }
+    Binding& z = x->b[zs];
+    z = saved[zs];
+    z.p = static_cast<char*>(z.p) + size_t(c0) * size_t(z.ld) * es;
+    z.cols = nc;
+    status = e.eval(x, st);  // adds its launches to x->last_launches
+    if (status != FX_OK) break;
+    if (cudaEventRecord(ev_out[i], st) != cudaSuccess || cudaStreamWaitEvent(down, ev_out[i], 0) != cudaSuccess) {
+      status = cuda_fail(cudaGetLastError(), "chunk events");
+      break;
+    }
+    status = copy_part(saved[zs], es, 0, host_out[0], c0, nc, cudaMemcpyDeviceToHost, down);
+  }
+  for (int k = 0; k < FX_MAX_SLOTS; ++k) x->b[k] = saved[k];
+  // the caller's stream resumes after the last copy down (or whatever was enqueued)
+  cudaEvent_t fin = x->chunk_ev[15];
+  if (cudaEventRecord(fin, down) == cudaSuccess) cudaStreamWaitEvent(st, fin, 0);
+  if (cudaEventRecord(ev_in[7], up) == cudaSuccess) cudaStreamWaitEvent(st, ev_in[7], 0);
+  *done = true;
+  return status;
+}
+
 fx_status fx_eval_host(fx_expr* x, const void* const* host_in, void* const* host_out, void* stream) {
   if (!x || !host_in || !host_out) return fail(FX_E_ARG, "null argument");
   const Entry& e = *x->e;
   FX_TRY(check_bound(x, 0, e.n_in + e.n_out));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < e.n_in; ++k)
+    if (!host_in[k] && x->b[k].rows * x->b[k].cols != 0) return fail(FX_E_ARG, "null host input %d", k);
+  for (int k = 0; k < e.n_out; ++k)
+    if (!host_out[k] && x->b[e.n_in + k].rows * x->b[e.n_in + k].cols != 0)
+      return fail(FX_E_ARG, "null host output %d", k);
+  {
+    bool done = false;
+    const fx_status s = eval_host_pipelined(x, host_in, host_out, st, x->b[e.n_in].cols, &done);
+    if (done || s != FX_OK) return s;
+  }
   for (int k = 0; k < e.n_in + e.n_out; ++k) {
     const Binding& b = x->b[k];
     const bool reduce_out = k >= e.n_in && e.kind != FX_KIND_ELEMENTWISE &&
