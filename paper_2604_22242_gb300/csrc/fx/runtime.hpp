@@ -60,7 +60,7 @@ struct fx_expr {
   fx::BatchCache* batch = nullptr;
   // fx_eval_host's copy streams and chunk events (created on first use)
   cudaStream_t copy_st[2] = {nullptr, nullptr};
-  cudaEvent_t chunk_ev[2 * 8 + 1] = {};
+  cudaEvent_t chunk_ev[2 * 8 + 2] = {};  // per chunk in / out, start, finish
 };
 
 namespace fx {
