@@ -52,6 +52,13 @@ METRIC = "fused-expr effective HBM GB/s (% of GB300 peak) and speedup vs unfused
 # valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {}
 
+# FP64-pipe instructions per output element of FP64 trees (per lane: DFMA,
+# DADD and DMUL each take one slot), counted with ncu
+# (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over
+# 4096^2 elements): exp, sqrt and division of the Z tree run as FMA
+# sequences on the FP64 pipe, which on GB300 is slower than HBM.
+FP64_PIPE_OPS = {("expr8192_f64", "Z"): 35}
+
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
@@ -464,7 +471,8 @@ def run_ours(args, rank, world):
         if world > 1:
             dist.barrier()
         clocks = clk.stop(t_start, t_end)
-        per_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+        per_all = {k: [a.elapsed_time(b) for a, b in v] for k, v in ev.items()}
+        per_ms = {k: statistics.mean(v) for k, v in per_all.items()}
         ms = t0.elapsed_time(t1)
         if flush:   # device time of the kernels alone (flushes excluded)
             ms = K * sum(per_ms.values())
@@ -516,7 +524,9 @@ def run_ours(args, rank, world):
         "pct_of_peak": round(100 * value / world / peak, 2),
         "pct_of_8tbs_spec": round(100 * value / world / 8000, 2),
         "vs_unfused": round(sum(u_ms.values()) / fused_u, 3) if u_ms else None,
-        "per_op": {k: {"ms": round(per_ms[k], 4), "bytes": next(o.bytes for o in ops if o.key == k),
+        "per_op": {k: {"ms": round(per_ms[k], 4), "median_ms": round(statistics.median(per_all[k]), 4),
+                       "min_ms": round(min(per_all[k]), 4),
+                       "bytes": next(o.bytes for o in ops if o.key == k),
                        "gbs": round(next(o.bytes for o in ops if o.key == k) / per_ms[k] / 1e6, 1),
                        "unfused_ms": round(u_ms[k], 4) if k in u_ms else None}
                    for k in per_ms},
@@ -528,9 +538,35 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if (args.workload, dom) in FP64_PIPE_OPS:
+        alu = fp64_roofline(fx, sp, args.workload, dom, dom_op, per_ms[dom], peak, storage, cfg)
+        if alu:
+            line["roofline"] = alu
     if e2e:
         line["e2e"] = e2e
     print(json.dumps(line), flush=True)
+
+
+def fp64_roofline(fx, sp, workload, dom, dom_op, ms, hbm_peak, storage, cfg):
+    """The ALU roofline of an FP64 tree when it binds before HBM: FP64-pipe
+    instructions per second (ncu count per element x elements / kernel time)
+    against the FMA rate measured now on this GPU (fx_fp64_fma_rate)."""
+    es = 8 if storage == "f64" else 4
+    n_el = cfg["rows"] * cfg["cols"]
+    ops = FP64_PIPE_OPS[(workload, dom)] * n_el
+    fma_rate = fx.fx_fp64_fma_rate(sp) / 2.0          # FMA (pipe slots) per second
+    t_alu = ops / fma_rate
+    t_hbm = dom_op.bytes / (hbm_peak * 1e9)
+    if t_alu <= t_hbm:
+        return None
+    achieved = ops / (ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fma_rate / 1e9, 2),
+            "peak_kind": "measured (fx_fp64_fma_rate, FP64 FMA chains on every SM)",
+            "unit": "G FP64-pipe op/s", "frac": round(achieved * 1e9 / fma_rate, 4),
+            "traffic": None, "kernel": dom,
+            "alg_ops_per_launch": ops, "ops_per_element": FP64_PIPE_OPS[(workload, dom)],
+            "avg_launch_ms": round(ms, 4),
+            "hbm_frac": round(dom_op.bytes / (ms / 1e3) / 1e9 / hbm_peak, 4)}
 
 
 def e2e_run(fx, torch, stream, sp, keep, storage, K, size):

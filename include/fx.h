@@ -226,6 +226,13 @@ fx_status fx_expr_sync_status(fx_expr* x, void* stream);
 
 /* ---- evaluation without device allocation ------------------------------ */
 
+/* Measured FP64 FMA throughput of the current device in flop/s (two flops
+ * per FMA): a short launch of independent FMA chains on every SM, timed
+ * with CUDA events on `stream` (synchronises it). The denominator of the
+ * ALU roofline of FP64 trees, whose exp, sqrt and division sequences run
+ * on the FP64 pipe. */
+fx_status fx_fp64_fma_rate(void* stream, double* flops_per_s);
+
 /* Bytes of the fixed device array behind fx_sqdiff_accu_f32_noalloc: room
  * for 4096 per-block partial sums (16 bytes each) and a completion ticket. */
 #define FX_NOALLOC_SCRATCH (4096 * 16 + 256)

@@ -268,6 +268,12 @@ def _materialise(n: Node, env):
     return np.broadcast_to(at(n, env, np.arange(r)[:, None], np.arange(c)[None, :]), (r, c))
 
 
+def _materialise_sigma(n: Node, env):
+    r, c = shape_of(n, env)
+    v, sg = at_sigma(n, env, np.arange(r)[:, None], np.arange(c)[None, :])
+    return np.broadcast_to(v, (r, c)), np.broadcast_to(sg, (r, c))
+
+
 def at(node, env, R, C):
     """Values of an element-wise tree at positions ``(R, C)`` of its logical
     matrix (``R``, ``C`` broadcastable integer index arrays).
@@ -353,7 +359,17 @@ def at_sigma(node, env, R, C):
         z = (a > n.args[1].value).astype(np.float64)
         return z, np.zeros_like(z)
     if _is_product(n):
-        raise ValueError("no error bound for a matrix product")
+        # dot products of length K summed in order: the standard forward
+        # bound |fl(x.y) - x.y| <= K u |x|.|y| (Higham, Accuracy and
+        # Stability of Numerical Algorithms, Sec. 3.1), plus the operands'
+        # own errors carried through the products
+        A, sA = _materialise_sigma(n.args[0], env)
+        B, sB = _materialise_sigma(n.args[1], env)
+        K = A.shape[1]
+        z = A @ B
+        s = sA @ np.abs(B) + np.abs(A) @ sB + K * (np.abs(A) @ np.abs(B))
+        R, C = np.broadcast_arrays(np.asarray(R), np.asarray(C))
+        return z[R, C], s[R, C]
     if op in BINARY:
         a, sa = at_sigma(n.args[0], env, R, C)
         b, sb = at_sigma(n.args[1], env, R, C)

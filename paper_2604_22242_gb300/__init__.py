@@ -19,7 +19,7 @@ __all__ = [
     "fx_list", "fx_expr_create", "fx_expr_destroy", "fx_expr_info", "fx_expr_slot_name",
     "fx_expr_bind", "fx_expr_set_scalar", "fx_expr_get_scalar", "fx_eval", "fx_eval_unfused",
     "fx_eval_host", "fx_eval_batch", "fx_eval_backward", "fx_tune", "fx_expr_launch_shape",
-    "fx_expr_set_launch_shape",
+    "fx_expr_set_launch_shape", "fx_fp64_fma_rate",
     "fx_expr_last_launches", "fx_expr_sync_status", "fx_last_error_string", "fx_status_string", "BatchItem",
     "colmajor", "bind_tensor", "Expr", "FusedLoss", "DTYPE_OF",
 ]
@@ -80,6 +80,7 @@ def lib():
         "fx_expr_launch_shape": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "fx_expr_set_launch_shape": (st, [vp, i32, i32, i32, i32]),
+        "fx_fp64_fma_rate": (st, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fx_expr_last_launches": (i32, [vp]),
         "fx_expr_sync_status": (st, [vp, vp]),
         "fx_last_error_string": (ctypes.c_char_p, []),
@@ -187,6 +188,13 @@ def fx_expr_launch_shape(h):
     _check(lib().fx_expr_launch_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                       ctypes.byref(d)))
     return a.value, b.value, c.value, d.value
+
+
+def fx_fp64_fma_rate(stream: int = 0) -> float:
+    """Measured FP64 FMA throughput of the current device, flop/s."""
+    v = ctypes.c_double()
+    _check(lib().fx_fp64_fma_rate(stream or None, ctypes.byref(v)))
+    return v.value
 
 
 def fx_expr_set_launch_shape(h, block: int, unroll: int, blocks_per_sm: int = 0,

@@ -68,7 +68,9 @@ def build(jobs: int | None = None, force: bool = False, verbose: bool = False) -
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + ".tmp"
-        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+        libdir = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+        cmd = ([nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs +
+               ["-L" + libdir, "-lcublas", "-Xlinker", "-rpath", "-Xlinker", libdir])
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"link failed:\n{p.stderr[-6000:]}")

@@ -241,5 +241,43 @@ struct SumSchur {
   }
 };
 
+// Fig. 1: Z = 2 X Y^T (a matrix product: a fusion boundary; the scalar
+// becomes the GEMM's alpha)
+struct GemmScale {
+  FX_DEF_COMMON("gemm_scale", "(* s0 (* X (t Y)))", 2, 1, 1, FX_KIND_ELEMENTWISE, ALL_DTYPES,
+                false, false)
+  static constexpr const char* slots[] = {"X", "Y", "Z"};
+  static constexpr double defaults[] = {2.0};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto X = in<0, T>(); auto Y = in<1, T>();
+    return s[0] * (X * trans(Y));
+  }
+};
+
+// A product with an element-wise remainder: the GEMM, then one fused pass
+// Z = sigmoid(s0 * (X * Y) + W)
+struct GemmEpilogue {
+  FX_DEF_COMMON("gemm_epilogue", "(sigmoid (+ (* s0 (* X Y)) W))", 3, 1, 1, FX_KIND_ELEMENTWISE,
+                dmask(FX_F32) | dmask(FX_BF16) | dmask(FX_F64), false, false)
+  static constexpr const char* slots[] = {"X", "Y", "W", "Z"};
+  static constexpr double defaults[] = {0.5};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto X = in<0, T>(); auto Y = in<1, T>(); auto W = in<2, T>();
+    return sigmoid(s[0] * (X * Y) + W);
+  }
+};
+
+// Sec. 4 chain: Z = A * B * C * D (left to right, three products)
+struct Chain {
+  FX_DEF_COMMON("chain", "(* (* (* A B) C) D)", 4, 1, 0, FX_KIND_ELEMENTWISE, dmask(FX_F32),
+                false, false)
+  static constexpr const char* slots[] = {"A", "B", "C", "D", "Z"};
+  static constexpr double defaults[] = {0.0};
+  template <class T> static FX_HD auto build(const double*) {
+    auto A = in<0, T>(); auto B = in<1, T>(); auto C = in<2, T>(); auto D = in<3, T>();
+    return A * B * C * D;
+  }
+};
+
 }  // namespace defs
 }  // namespace fx

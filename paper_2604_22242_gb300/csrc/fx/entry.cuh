@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "batch.cuh"
+#include "gemm.cuh"
 #include "unfused.cuh"
 
 namespace fx {
@@ -79,13 +80,13 @@ inline fx_status run_tune(fx_expr* x, int mode, cudaStream_t st, EvalFn ev, int 
 }
 
 // Access mode of every input slot of a leaf list (-1: read in two modes).
-template <class LL> struct SlotModes {
+template <class LL, bool ALL_MIXED = false> struct SlotModes {
   signed char m[FX_MAX_SLOTS];
   constexpr SlotModes() : m{} {
     for (int k = 0; k < FX_MAX_SLOTS; ++k) m[k] = -2;
     fill<0>();
     for (int k = 0; k < FX_MAX_SLOTS; ++k)
-      if (m[k] == -2) m[k] = 0;
+      if (m[k] == -2 || ALL_MIXED) m[k] = ALL_MIXED ? -1 : 0;
   }
   template <int I> constexpr void fill() {
     if constexpr (I < tl_size<LL>::value) {
@@ -99,18 +100,22 @@ template <class LL> struct SlotModes {
 
 template <class Def, class T> struct Inst {
   static auto root(const fx_expr* x) { return normalize(Def::template build<T>(x->scal)); }
+  using Root = std::decay_t<decltype(normalize(Def::template build<T>(nullptr)))>;
+  static constexpr bool prods = has_prod_any<Root>::value;
   static fx_status eval(fx_expr* x, cudaStream_t st) {
-    return run_root<T>(run_of(x, st), root(x), Def::kind);
+    if constexpr (prods) return run_with_prods<T, Def::n_in>(x, root(x), Def::kind, st, false);
+    else return run_root<T>(run_of(x, st), root(x), Def::kind);
   }
   static fx_status unfused(fx_expr* x, cudaStream_t st) {
-    return run_unfused<T>(x, root(x), Def::kind, st);
+    if constexpr (prods) return run_with_prods<T, Def::n_in>(x, root(x), Def::kind, st, true);
+    else return run_unfused<T>(x, root(x), Def::kind, st);
   }
   static fx_status backward(fx_expr* x, const void* g, void* const* gp, cudaStream_t st) {
-    if constexpr (Def::differentiable) return run_backward<T>(x, root(x), g, gp, st);
+    if constexpr (Def::differentiable && !prods) return run_backward<T>(x, root(x), g, gp, st);
     else return fail(FX_E_UNSUPPORTED, "no fused backward");
   }
   static fx_status batch(fx_expr* x, int64_t n, const fx_batch_item* it, cudaStream_t st, int g) {
-    if constexpr (Def::batchable) return run_batch<T, Def::n_in, Def::kind>(x, root(x), n, it, st, g);
+    if constexpr (Def::batchable && !prods) return run_batch<T, Def::n_in, Def::kind>(x, root(x), n, it, st, g);
     else return fail(FX_E_UNSUPPORTED, "no batched entry");
   }
   // The search times every kernel variant (pipeline 0, 1, 2) with every
@@ -118,8 +123,10 @@ template <class Def, class T> struct Inst {
   static fx_status tune(fx_expr* x, int mode, cudaStream_t st) {
     return run_tune(x, mode, st, &eval, 3);
   }
-  using Root = std::decay_t<decltype(normalize(Def::template build<T>(nullptr)))>;
-  static constexpr SlotModes<leaves_t<typename root_of<Root>::inner>> modes{};
+  // input slots of trees with products are consumed by GEMMs: mode -1
+  // (no column-chunked host pipeline)
+  static constexpr SlotModes<leaves_t<typename root_of<typename Lift<Root, T, Def::n_in>::type>::inner>,
+                             prods> modes{};
   static Entry entry() {
     return Entry{Def::name, Def::formula, dtype_of<T>::value, Def::n_in, Def::n_out, Def::n_scal,
                  fx_kind(Def::kind), Def::slots, Def::defaults, &eval, &unfused,

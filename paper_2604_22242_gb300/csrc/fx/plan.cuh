@@ -14,8 +14,8 @@
 //      accu / norm root                                -> same, with a fused
 //                                                         reduction epilogue (A5)
 //      sum / max along a dimension                     -> dim reduction (A6)
-//    A matrix product node is a fusion boundary (has_prod_v): the fused
-//    kernels refuse such a tree; its operands must be materialised first.
+//    A matrix product node is a fusion boundary (has_prod_v): gemm.cuh
+//    computes it first into a temporary, bound as a plain leaf of the rest.
 #pragma once
 
 #include "expr.cuh"
@@ -132,6 +132,20 @@ template <class Op, class E, bool F> struct Norm<SL<Op, E>, F> {
 template <class Op, class E, bool F> struct Norm<SR<Op, E>, F> {
   using type = SR<Op, typename Norm<E, F>::type>;
   static FX_HD type make(const SR<Op, E>& x) { return {{}, Norm<E, F>::make(x.e), x.s}; }
+};
+// Products: normalise the operands; a transposed product swaps and
+// transposes them ((L R)^T = R^T L^T).
+template <class L, class R> struct Norm<Prod<L, R>, false> {
+  using type = Prod<typename Norm<L, false>::type, typename Norm<R, false>::type>;
+  static FX_HD type make(const Prod<L, R>& x) {
+    return {{}, Norm<L, false>::make(x.l), Norm<R, false>::make(x.r)};
+  }
+};
+template <class L, class R> struct Norm<Prod<L, R>, true> {
+  using type = Prod<typename Norm<R, true>::type, typename Norm<L, true>::type>;
+  static FX_HD type make(const Prod<L, R>& x) {
+    return {{}, Norm<R, true>::make(x.r), Norm<L, true>::make(x.l)};
+  }
 };
 // Reductions: normalise the operand (a reduction is never transposed here).
 template <class E> struct Norm<Accu<E>, false> {

@@ -55,6 +55,7 @@ struct fx_expr {
   fx::Workspace ws;
   fx::Workspace ws_tmp;  // unfused intermediates
   fx::Workspace ws_err;  // error word of bounded waits (kErrTimeout)
+  fx::Workspace ws_gemm; // matrix products of a tree (fusion boundaries)
   fx::Tune tune;
   int last_launches = 0;
   fx::BatchCache* batch = nullptr;

@@ -145,11 +145,14 @@ template <class E> struct reroot<Norm2<E>> { template <class L> using type = Nor
 template <class E, int D> struct reroot<SumDim<E, D>> { template <class L> using type = SumDim<L, D>; };
 template <class E, int D> struct reroot<MaxDim<E, D>> { template <class L> using type = MaxDim<L, D>; };
 
+// `over`: the binding table and input count to use instead of the object's
+// (trees whose matrix products were computed into temporaries first).
 template <class T, class Root>
-fx_status run_unfused(fx_expr* x, const Root& root, int kind, cudaStream_t st) {
+fx_status run_unfused(fx_expr* x, const Root& root, int kind, cudaStream_t st,
+                      const Run* over = nullptr) {
   using E = typename root_of<Root>::inner;
   using LL = leaves_t<E>;
-  Run r = run_of(x, st);
+  Run r = over ? *over : run_of(x, st);
   const E& e = inner_of(root);
   int64_t R = 0, C = 0;
   if (!infer_shape<LL>(r.b, R, C)) return fail(FX_E_SHAPE, "no matrix leaf to take the shape from");

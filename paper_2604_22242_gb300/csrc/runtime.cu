@@ -219,6 +219,7 @@ fx_status fx_expr_destroy(fx_expr* x) {
   x->ws.release();
   x->ws_tmp.release();
   x->ws_err.release();
+  x->ws_gemm.release();
   delete x;
   return FX_OK;
 }

@@ -38,6 +38,10 @@ TREES = {
     "swish": "(/ X (+ 1 (exp (neg (* {s0} X)))))",
     "gelu": "(% (/ X 2) (+ 1 (tanh (* {s0} (+ X (* {s1} (pow X 3)))))))",
     "sum_schur": "(% (+ A B) (+ C D))",
+    # matrix products (Fig. 1, a product with an element-wise remainder, Sec. 4 chain)
+    "gemm_scale": "(* {s0} (* X (t Y)))",
+    "gemm_epilogue": "(sigmoid (+ (* {s0} (* X Y)) W))",
+    "chain": "(* (* (* A B) C) D)",
 }
 for _n in range(2, 17):
     _t = "A1"
@@ -46,7 +50,8 @@ for _n in range(2, 17):
     TREES[f"add{_n}"] = _t
 DEFAULT_SCALARS = {"schur_exp_trans": [3.5], "schur_sqrt_sigmoid": [1.0],
                    "schur_trans_accu": [0.5], "expr1": [2.0], "expr2": [0.75, 2.0], "relu": [0.0],
-                   "sigmoid": [1.0], "swish": [1.0], "gelu": [0.7978845608028654, 0.044715]}
+                   "sigmoid": [1.0], "swish": [1.0], "gelu": [0.7978845608028654, 0.044715],
+                   "gemm_scale": [2.0], "gemm_epilogue": [0.5]}
 SLOTS = {
     "schur_exp_trans": ["A", "B", "C", "D"],
     "sqdiff_accu": ["A", "B"],
@@ -58,6 +63,7 @@ SLOTS = {
     "sigmoid_sqloss": ["X", "W", "Y", "b"],
     "expr1": ["X", "Y"], "expr2": ["A", "B", "C", "D"], "relu": ["X"], "sigmoid": ["X"],
     "swish": ["X"], "gelu": ["X"], "sum_schur": ["A", "B", "C", "D"],
+    "gemm_scale": ["X", "Y"], "gemm_epilogue": ["X", "Y", "W"], "chain": ["A", "B", "C", "D"],
 }
 for _n in range(2, 17):
     SLOTS[f"add{_n}"] = [f"A{_k}" for _k in range(1, _n + 1)]
@@ -70,7 +76,7 @@ TOL_TRANS = {"f64": 1e-13, "f32": 1e-5, "bf16": 8e-3, "f16": 1e-3}
 # compensated FP32 accumulation, so they are held to the FP32 reduction bound
 TOL_RED = {"f64": 1e-13, "f32": 1e-5, "bf16": 1e-5, "f16": 1e-5}
 HAS_TRANSCENDENTAL = {"schur_exp_trans", "schur_sqrt_sigmoid", "sigmoid_sqloss", "expr2",
-                      "sigmoid", "swish", "gelu"}
+                      "sigmoid", "swish", "gelu", "gemm_epilogue"}
 
 
 def tree_of(name, scalars=None):

@@ -355,6 +355,69 @@ def test_sigma_bounds_float32_rounding(tree):
     assert np.median(s[ok] / np.maximum(np.abs(z[ok]), 1e-30)) < 50
 
 
+def _f32_product_tree(node, env):
+    """Full-matrix FP32 evaluation where matrix products are summed in k
+    order, one float32 rounding per multiply and per add (a plain loop over
+    the inner dimension)."""
+    n = oracle.parse(node)
+    f = np.float32
+    if n.op == "leaf":
+        b = env[n.name]
+        return oexpr._leaf_values(b, np.arange(b.rows)[:, None], np.arange(b.cols)[None, :]).astype(f)
+    if n.op == "t":
+        return _f32_product_tree(n.args[0], env).T.copy()
+    if n.op == "*" and n.args[0].op == "num":
+        return (f(n.args[0].value) * _f32_product_tree(n.args[1], env)).astype(f)
+    if n.op == "*":
+        A = _f32_product_tree(n.args[0], env)
+        B = _f32_product_tree(n.args[1], env)
+        acc = np.zeros((A.shape[0], B.shape[1]), dtype=f)
+        for k in range(A.shape[1]):
+            acc = (acc + (A[:, k:k + 1] * B[k:k + 1, :]).astype(f)).astype(f)
+        return acc
+    a = _f32_product_tree(n.args[0], env)
+    b = _f32_product_tree(n.args[1], env)
+    return {"+": lambda: a + b, "-": lambda: a - b, "%": lambda: a * b}[n.op]().astype(f)
+
+
+@pytest.mark.parametrize("tree", ["(* 2 (* A (t D)))", "(* (* A B) C)",
+                                  "(+ (* 0.5 (* A B)) C)", "(- (* (t D) B) A)"])
+def test_sigma_bounds_float32_matrix_products(tree):
+    """The product bound (K u |A||B| plus carried operand errors) covers a
+    k-ordered FP32 summation, the worst order for a dot product."""
+    r = 40
+    env = synth.operands(23, [("A", r, r), ("B", r, r), ("C", r, r), ("D", r, r)], "f32",
+                         "normal")
+    z, s = oracle.evaluate_sigma(tree, env)
+    z32 = _f32_product_tree(tree, env).astype(np.float64)
+    u = 2.0 ** -24
+    assert np.all(np.abs(z32 - z) <= 4 * u * s)
+    assert np.all(s > 0)
+
+
+def test_matrix_product_closed_forms():
+    """ones(n, k) * ones(k, m) = k everywhere, with sigma = k * k; (A B)^T =
+    B^T A^T exactly in FP64 for small integers."""
+    n, k, m = 6, 9, 5
+    env = {"O1": synth.Buffer(np.ones(n * k), n, k, n, "f64"),
+           "O2": synth.Buffer(np.ones(k * m), k, m, k, "f64")}
+    z, s = oracle.evaluate_sigma("(* O1 O2)", env)
+    assert np.all(z == k) and np.all(s == k * k)
+    rng = np.random.default_rng(3)
+    env2 = {"A": synth.Buffer(rng.integers(-9, 10, 4 * 7).astype(np.float64), 4, 7, 4, "f64"),
+            "B": synth.Buffer(rng.integers(-9, 10, 7 * 3).astype(np.float64), 7, 3, 7, "f64")}
+    ab_t = oracle.evaluate("(t (* A B))", env2)
+    bt_at = oracle.evaluate("(* (t B) (t A))", env2)
+    assert np.array_equal(ab_t, bt_at)
+    # brute-force triple loop
+    A = env2["A"].data.reshape(7, 4).T
+    B = env2["B"].data.reshape(3, 7).T
+    ab = oracle.evaluate("(* A B)", env2)
+    for i in range(4):
+        for j in range(3):
+            assert ab[i, j] == sum(A[i, q] * B[q, j] for q in range(7))
+
+
 def test_sigma_reduction_rules():
     env = synth.operands(22, [("A", 40, 30), ("B", 40, 30)], "f32", "normal")
     v, s = oracle.evaluate_sigma("(accu (% A B))", env)
