@@ -161,7 +161,7 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
             b = env[s]
             _bind(fx, h, k, d[s], b.rows, b.cols, b.ld)
             if s not in ins[:k]:          # a leaf read twice is read once (fusion)
-                nb += b.rows * b.cols * es
+                nb += b.rows * b.cols * {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[b.storage]
         if kind == "Z":
             o = torch.empty(R * C, dtype=tdt, device=dev)
             _bind(fx, h, len(ins), o, R, C, R)
@@ -217,17 +217,21 @@ def workload(name, fx, torch, dev, sp, keep, size=8192, count=4096):
     if name == "batch4096":
         return batch_workload(fx, torch, dev, sp, keep, count)
     if name == "suite10k":
-        R = C = 10000
+        R = C = 10000 if size == 8192 else size
         env = synth.operands(4, [(f"A{k}", R, C) for k in range(1, 17)], "f32", "uniform")
+        env.update(synth.operands(5, [("P1", R, C), ("P2", R, C)], "f32", "positive"))
+        env.update(synth.operands(6, [("Y64", R, C)], "f64", "normal"))
         trees = [(f"add{n}", f"add{n}", [f"A{k}" for k in range(1, n + 1)], "Z")
                  for n in range(2, 17)]
         trees += [("expr1", "expr1", ["A1", "A2"], "Z"),
                   ("expr2", "expr2", ["A1", "A2", "A3", "A4"], "Z"),
+                  ("expr3", "expr3", ["P1", "Y64", "P2"], "Z"),
                   ("relu", "relu", ["A1"], "Z"), ("sigmoid", "sigmoid", ["A1"], "Z"),
                   ("swish", "swish", ["A1"], "Z"), ("gelu", "gelu", ["A1"], "Z")]
         cfg = {"workload": "Sec. 4 suite at 10000x10000 FP32: add-N (N=2..16), expr1, expr2, "
-                           "relu, sigmoid, swish, gelu", "rows": R, "cols": C,
-               "inputs": "A1..A16 U[-1,1], seed 4, column-major",
+                           "expr3 (FP64 Y), relu, sigmoid, swish, gelu", "rows": R, "cols": C,
+               "inputs": "A1..A16 U[-1,1], seed 4; P1, P2 U[0.5,2], seed 5; Y64 FP64 N(0,1), "
+                         "seed 6; column-major",
                "l2": "inputs larger than L2 (400 MB each), no flush"}
         return _expr_ops(fx, torch, dev, sp, trees, "f32", env, R, C, keep), cfg, "add16", False, "f32"
     if name in ("loss8192_f32", "loss8192_bf16"):
@@ -619,7 +623,8 @@ def main():
                              "prec16384_f16", "batch4096", "loss8192_f32", "loss8192_bf16",
                              "suite10k"])
     ap.add_argument("--size", type=int, default=8192,
-                    help="rows = cols of the expr8192 and loss8192 workloads")
+                    help="rows = cols of the expr8192 and loss8192 workloads (other values than "
+                         "8192 also resize prec16384_* and suite10k, for profiling)")
     ap.add_argument("--count", type=int, default=4096, help="matrices of the batch4096 workload")
     ap.add_argument("--tune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--shape", default="",

@@ -110,6 +110,12 @@ fx_status fx_expr_info(const fx_expr* x, int* n_inputs, int* n_outputs, int* n_s
 /* Name of slot `slot` (inputs first, then outputs), e.g. "A" or "Z". */
 fx_status fx_expr_slot_name(const fx_expr* x, int slot, const char** name);
 
+/* Storage type of a slot's buffer. Every slot of a tree has the tree's
+ * storage type (the fx_expr_create argument) except inputs a definition
+ * fixes otherwise (expr3's Y is FP64 in an FP32 tree, read as its FP32
+ * rounding); reduction outputs are FP32 (FP64 for FP64 trees). */
+fx_status fx_expr_slot_dtype(const fx_expr* x, int slot, fx_dtype* dtype);
+
 /* Binds a device buffer to a slot: `rows` x `cols`, column-major with
  * leading dimension `ld` (>= rows; ld may be anything >= 1 for rows <= 1).
  * The element type is the expression's storage type for inputs and
@@ -232,6 +238,12 @@ fx_status fx_expr_sync_status(fx_expr* x, void* stream);
  * ALU roofline of FP64 trees, whose exp, sqrt and division sequences run
  * on the FP64 pipe. */
 fx_status fx_fp64_fma_rate(void* stream, double* flops_per_s);
+
+/* Self-test of the bounded waits: one warp waits on a shared-memory
+ * mbarrier that nothing arrives on, gives up after 1000 polls and records
+ * the timeout; *word receives the error word (1 = a wait gave up). The
+ * kernel always finishes; synchronises `stream`. */
+fx_status fx_selftest_wait_timeout(void* stream, unsigned int* word);
 
 /* Bytes of the fixed device array behind fx_sqdiff_accu_f32_noalloc: room
  * for 4096 per-block partial sums (16 bytes each) and a completion ticket. */

@@ -11,6 +11,7 @@ Operators (Sec. 4 expression suite and Sec. 3 functions):
     *              number times matrix (scalar scale); matrix times matrix is
                    a matrix product, a fusion boundary
     neg exp log sqrt abs square sigmoid tanh      unary
+    f32 X          X rounded to FP32 (round to nearest even): conv_to<fmat>
     pow X k        X to the number k;     gt X s   1 where X > s, else 0
     t X            transpose (Sec. 3: row and col swap before the access)
     each_col b     b (rows x 1) repeated over every column
@@ -35,12 +36,12 @@ import synth
 from .sums import neumaier, neumaier_axis
 
 BINARY = {"+", "-", "%", "/", "*"}
-UNARY = {"neg", "exp", "log", "sqrt", "abs", "square", "sigmoid", "tanh"}
+UNARY = {"neg", "exp", "log", "sqrt", "abs", "square", "sigmoid", "tanh", "f32"}
 REDUCTIONS = {"accu", "sum", "max", "norm"}
 _EXACT_UNARY = {"neg", "abs"}
 
 _ARITY = {"neg": 1, "exp": 1, "log": 1, "sqrt": 1, "abs": 1, "square": 1, "sigmoid": 1,
-          "tanh": 1, "t": 1, "each_col": 1, "each_row": 1, "accu": 1, "norm": 1,
+          "tanh": 1, "f32": 1, "t": 1, "each_col": 1, "each_row": 1, "accu": 1, "norm": 1,
           "pow": 2, "gt": 2, "sum": 2, "max": 2, "+": 2, "-": 2, "%": 2, "/": 2, "*": 2}
 
 
@@ -225,6 +226,8 @@ def _apply_unary(op, a):
             return 1.0 / (1.0 + np.exp(-a))
         if op == "tanh":
             return np.tanh(a)
+        if op == "f32":                          # Sec. 4 expr3: conv_to<fmat>, round to nearest
+            return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
     raise ValueError(op)
 
 
@@ -247,6 +250,8 @@ def _unary_deriv(op, a, z):
             return z * (1.0 - z)
         if op == "tanh":
             return 1.0 - z * z
+        if op == "f32":
+            return np.ones_like(a)
     raise ValueError(op)
 
 

@@ -19,7 +19,8 @@ __all__ = [
     "fx_list", "fx_expr_create", "fx_expr_destroy", "fx_expr_info", "fx_expr_slot_name",
     "fx_expr_bind", "fx_expr_set_scalar", "fx_expr_get_scalar", "fx_eval", "fx_eval_unfused",
     "fx_eval_host", "fx_eval_batch", "fx_eval_backward", "fx_tune", "fx_expr_launch_shape",
-    "fx_expr_set_launch_shape", "fx_fp64_fma_rate",
+    "fx_expr_set_launch_shape", "fx_fp64_fma_rate", "fx_expr_slot_dtype",
+    "fx_selftest_wait_timeout",
     "fx_expr_last_launches", "fx_expr_sync_status", "fx_last_error_string", "fx_status_string", "BatchItem",
     "colmajor", "bind_tensor", "Expr", "FusedLoss", "DTYPE_OF",
 ]
@@ -81,6 +82,8 @@ def lib():
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "fx_expr_set_launch_shape": (st, [vp, i32, i32, i32, i32]),
         "fx_fp64_fma_rate": (st, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "fx_expr_slot_dtype": (st, [vp, i32, ctypes.POINTER(i32)]),
+        "fx_selftest_wait_timeout": (st, [vp, ctypes.POINTER(ctypes.c_uint)]),
         "fx_expr_last_launches": (i32, [vp]),
         "fx_expr_sync_status": (st, [vp, vp]),
         "fx_last_error_string": (ctypes.c_char_p, []),
@@ -188,6 +191,20 @@ def fx_expr_launch_shape(h):
     _check(lib().fx_expr_launch_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                       ctypes.byref(d)))
     return a.value, b.value, c.value, d.value
+
+
+def fx_expr_slot_dtype(h, slot: int) -> int:
+    """Storage type code (FX_F32, FX_F64, FX_BF16, FX_F16) of a slot's buffer."""
+    v = ctypes.c_int()
+    _check(lib().fx_expr_slot_dtype(h, slot, ctypes.byref(v)))
+    return v.value
+
+
+def fx_selftest_wait_timeout(stream: int = 0) -> int:
+    """Error word after a bounded wait that nothing releases (1 expected)."""
+    v = ctypes.c_uint()
+    _check(lib().fx_selftest_wait_timeout(stream or None, ctypes.byref(v)))
+    return v.value
 
 
 def fx_fp64_fma_rate(stream: int = 0) -> float:

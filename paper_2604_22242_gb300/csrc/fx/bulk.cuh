@@ -60,8 +60,8 @@ FX_D bool try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for phase `parity` of `bar`; false (and the error recorded) on timeout.
-FX_D bool wait(uint64_t* bar, uint32_t parity, unsigned int* err) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+FX_D bool wait(uint64_t* bar, uint32_t parity, unsigned int* err, uint32_t limit = kSpinLimit) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (try_wait(bar, parity)) return true;
   if (err) atomicOr(err, kErrTimeout);
   return false;

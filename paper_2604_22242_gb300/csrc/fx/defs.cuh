@@ -228,6 +228,19 @@ struct Gelu {
   }
 };
 
+// expr3 (Sec. 4): Z = 1 / (X % conv_to<fmat>(Y) + log(log(X + 2) % W)),
+// Y stored in FP64: a float tree reads a double leaf as its FP32 rounding.
+struct Expr3 {
+  FX_DEF_COMMON("expr3", "(/ 1 (+ (% X (f32 Y)) (log (% (log (+ X 2)) W))))", 3, 1, 0,
+                FX_KIND_ELEMENTWISE, dmask(FX_F32), false, false)
+  static constexpr const char* slots[] = {"X", "Y", "W", "Z"};
+  static constexpr double defaults[] = {0.0};
+  template <class T> static FX_HD auto build(const double*) {
+    auto X = in<0, T>(); auto Y = in<1, double>(); auto W = in<2, T>();
+    return 1.0 / (X % Y + log(log(X + 2.0) % W));
+  }
+};
+
 // (A + B) % (C + D): diagsum when bound to the diagonal views X.diag(-1),
 // X.diag(1), Y.diag(-1), Y.diag(1) (1 x n leaves with ld = parent ld + 1)
 struct SumSchur {

@@ -80,10 +80,16 @@ inline fx_status run_tune(fx_expr* x, int mode, cudaStream_t st, EvalFn ev, int 
 }
 
 // Access mode of every input slot of a leaf list (-1: read in two modes).
+// Access mode and storage type of every input slot of a leaf list (mode
+// -1: read in two modes; type -1: not a leaf of the list).
 template <class LL, bool ALL_MIXED = false> struct SlotModes {
   signed char m[FX_MAX_SLOTS];
-  constexpr SlotModes() : m{} {
-    for (int k = 0; k < FX_MAX_SLOTS; ++k) m[k] = -2;
+  signed char dt[FX_MAX_SLOTS];
+  constexpr SlotModes() : m{}, dt{} {
+    for (int k = 0; k < FX_MAX_SLOTS; ++k) {
+      m[k] = -2;
+      dt[k] = -1;
+    }
     fill<0>();
     for (int k = 0; k < FX_MAX_SLOTS; ++k)
       if (m[k] == -2 || ALL_MIXED) m[k] = ALL_MIXED ? -1 : 0;
@@ -93,6 +99,7 @@ template <class LL, bool ALL_MIXED = false> struct SlotModes {
       using L = typename tl_at<LL, I>::type;
       const signed char md = static_cast<signed char>(L::mode);
       m[L::slot] = (m[L::slot] == -2 || m[L::slot] == md) ? md : static_cast<signed char>(-1);
+      dt[L::slot] = static_cast<signed char>(dtype_of<typename L::elem>::value);
       fill<I + 1>();
     }
   }
@@ -131,7 +138,7 @@ template <class Def, class T> struct Inst {
     return Entry{Def::name, Def::formula, dtype_of<T>::value, Def::n_in, Def::n_out, Def::n_scal,
                  fx_kind(Def::kind), Def::slots, Def::defaults, &eval, &unfused,
                  Def::batchable ? &batch : nullptr, Def::differentiable ? &backward : nullptr,
-                 &tune, modes.m};
+                 &tune, modes.m, modes.dt};
   }
 };
 

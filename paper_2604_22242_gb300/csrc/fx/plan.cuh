@@ -77,15 +77,17 @@ template <class H, class... Ts, int M> struct tl_has_mode<TL<H, Ts...>, M> {
   static constexpr bool value = H::mode == M || tl_has_mode<TL<Ts...>, M>::value;
 };
 
-// Compute type: double if any leaf stores double, else float.
-template <class L> struct tl_any_double;
-template <> struct tl_any_double<TL<>> { static constexpr bool value = false; };
-template <class H, class... Ts> struct tl_any_double<TL<H, Ts...>> {
+// Compute type: double if every leaf stores double, else float. A double
+// leaf in a float tree is read as its FP32 rounding (round to nearest), the
+// conv_to<fmat> of the Sec. 4 expression expr3.
+template <class L> struct tl_all_double;
+template <> struct tl_all_double<TL<>> { static constexpr bool value = true; };
+template <class H, class... Ts> struct tl_all_double<TL<H, Ts...>> {
   static constexpr bool value =
-      std::is_same<typename H::elem, double>::value || tl_any_double<TL<Ts...>>::value;
+      std::is_same<typename H::elem, double>::value && tl_all_double<TL<Ts...>>::value;
 };
 template <class E>
-using ct_of = std::conditional_t<tl_any_double<leaves_t<E>>::value, double, float>;
+using ct_of = std::conditional_t<tl_all_double<leaves_t<E>>::value, double, float>;
 
 // Widest storage element among the leaves (sets the vector width).
 template <class L> struct tl_max_elem;

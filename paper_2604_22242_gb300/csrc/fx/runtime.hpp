@@ -90,7 +90,15 @@ struct Entry {
   // expr.cuh: 0 plain, 1 transposed, 2 each_col vector, 3 each_row vector);
   // -1 for a slot read in two modes
   const signed char* slot_modes;
+  // storage type of each input slot (-1: the entry's storage type)
+  const signed char* slot_dtypes;
 };
+
+// Storage type of slot k of an entry (outputs: the entry's storage type;
+// reduction outputs are the reduce type, see reduce_bytes).
+inline fx_dtype slot_dtype(const Entry& e, int k) {
+  return (k < e.n_in && e.slot_dtypes[k] >= 0) ? fx_dtype(e.slot_dtypes[k]) : e.storage;
+}
 
 std::vector<Entry>& registry();
 struct Registrar {

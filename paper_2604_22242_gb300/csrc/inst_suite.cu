@@ -5,6 +5,7 @@ namespace fx {
 namespace defs {
 FX_REGISTER(Expr1)
 FX_REGISTER(Expr2)
+FX_REGISTER(Expr3)
 FX_REGISTER(Relu)
 FX_REGISTER(SigmoidExpr)
 FX_REGISTER(Swish)

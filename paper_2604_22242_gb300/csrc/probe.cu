@@ -8,6 +8,7 @@
 // over the CUDA-event time of the launch.
 #include <cuda_runtime.h>
 
+#include "fx/bulk.cuh"
 #include "fx/runtime.hpp"
 
 namespace fx {
@@ -29,10 +30,38 @@ __global__ void __launch_bounds__(256) k_fp64_fma(double* out, int iters, double
   if (s == 12345.678) out[blockIdx.x] = s;  // keeps the chains live; never true for a, b below
 }
 
+// One warp waits on an mbarrier that nothing arrives on, with a short poll
+// limit: every lane must give up and record the timeout, and the kernel
+// must finish (the failure path of the pipelines' bounded waits).
+__global__ void k_wait_timeout(unsigned int* err, uint32_t polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_mbar_init();
+  }
+  __syncwarp();
+  tma::wait(&bar, 0, err, polls);
+}
+
 }  // namespace
 }  // namespace fx
 
 using namespace fx;
+
+extern "C" fx_status fx_selftest_wait_timeout(void* stream, unsigned int* word) {
+  if (!word) return fail(FX_E_ARG, "null output");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned int* err = nullptr;
+  FX_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&err), sizeof(unsigned int), st));
+  FX_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
+  k_wait_timeout<<<1, 32, 0, st>>>(err, 1000);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(word, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(err, st);
+  if (e != cudaSuccess) return cuda_fail(e, "wait-timeout self-test");
+  return FX_OK;
+}
 
 extern "C" fx_status fx_fp64_fma_rate(void* stream, double* flops_per_s) {
   if (!flops_per_s) return fail(FX_E_ARG, "null output");

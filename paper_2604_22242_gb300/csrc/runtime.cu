@@ -241,6 +241,16 @@ fx_status fx_expr_slot_name(const fx_expr* x, int slot, const char** name) {
   return FX_OK;
 }
 
+fx_status fx_expr_slot_dtype(const fx_expr* x, int slot, fx_dtype* dtype) {
+  if (!x || !dtype) return fail(FX_E_ARG, "null argument");
+  const Entry& e = *x->e;
+  if (slot < 0 || slot >= e.n_in + e.n_out) return fail(FX_E_ARG, "slot %d out of range", slot);
+  const bool reduce_out = slot >= e.n_in && e.kind != FX_KIND_ELEMENTWISE &&
+                          !(e.kind == FX_KIND_MULTI && slot == e.n_in);
+  *dtype = reduce_out ? (e.storage == FX_F64 ? FX_F64 : FX_F32) : slot_dtype(e, slot);
+  return FX_OK;
+}
+
 fx_status fx_expr_bind(fx_expr* x, int slot, void* dev_ptr, int64_t rows, int64_t cols, int64_t ld) {
   if (!x) return fail(FX_E_ARG, "null expression");
   const Entry& e = *x->e;
@@ -250,7 +260,7 @@ fx_status fx_expr_bind(fx_expr* x, int slot, void* dev_ptr, int64_t rows, int64_
   if (rows * cols > 0 && !dev_ptr) return fail(FX_E_ARG, "null pointer for a non-empty buffer");
   const bool reduce_out = slot >= e.n_in && e.kind != FX_KIND_ELEMENTWISE &&
                           !(e.kind == FX_KIND_MULTI && slot == e.n_in);
-  const size_t es = reduce_out ? reduce_bytes(e.storage) : storage_bytes(e.storage);
+  const size_t es = reduce_out ? reduce_bytes(e.storage) : storage_bytes(slot_dtype(e, slot));
   if (reinterpret_cast<uintptr_t>(dev_ptr) % es != 0)
     return fail(FX_E_ALIGN, "slot %d: pointer not aligned to its %zu-byte element", slot, es);
   Binding& b = x->b[slot];
@@ -369,10 +379,11 @@ static fx_status eval_host_pipelined(fx_expr* x, const void* const* host_in, voi
       const Binding& b = saved[k];
       const int md = e.slot_modes[k];
       if (b.rows * b.cols == 0) continue;
+      const size_t ek = storage_bytes(slot_dtype(e, k));
       if (md == 0 || md == 1) {
-        status = copy_part(b, es, md, const_cast<void*>(host_in[k]), c0, nc, cudaMemcpyHostToDevice, up);
+        status = copy_part(b, ek, md, const_cast<void*>(host_in[k]), c0, nc, cudaMemcpyHostToDevice, up);
       } else if (i == 0) {  // vectors: once, whole
-        status = copy_part(b, es, 0, const_cast<void*>(host_in[k]), 0, b.cols, cudaMemcpyHostToDevice, up);
+        status = copy_part(b, ek, 0, const_cast<void*>(host_in[k]), 0, b.cols, cudaMemcpyHostToDevice, up);
       }
     }
     if (status != FX_OK) break;
@@ -386,15 +397,16 @@ static fx_status eval_host_pipelined(fx_expr* x, const void* const* host_in, voi
       Binding& v = x->b[k];
       v = saved[k];
       const int md = e.slot_modes[k];
+      const size_t ek = storage_bytes(slot_dtype(e, k));
       if (md == 0) {
-        v.p = static_cast<char*>(v.p) + size_t(c0) * size_t(v.ld) * es;
+        v.p = static_cast<char*>(v.p) + size_t(c0) * size_t(v.ld) * ek;
         v.cols = nc;
       } else if (md == 1) {
-        v.p = static_cast<char*>(v.p) + size_t(c0) * es;
+        v.p = static_cast<char*>(v.p) + size_t(c0) * ek;
         v.rows = nc;
       } else if (md == 3) {
         const int64_t stride = v.rows == 1 ? v.ld : 1;
-        v.p = static_cast<char*>(v.p) + size_t(c0 * stride) * es;
+        v.p = static_cast<char*>(v.p) + size_t(c0 * stride) * ek;
         if (v.rows == 1) v.cols = nc;
         else v.rows = nc;
       }
@@ -439,7 +451,7 @@ fx_status fx_eval_host(fx_expr* x, const void* const* host_in, void* const* host
     const Binding& b = x->b[k];
     const bool reduce_out = k >= e.n_in && e.kind != FX_KIND_ELEMENTWISE &&
                             !(e.kind == FX_KIND_MULTI && k == e.n_in);
-    const size_t es = reduce_out ? reduce_bytes(e.storage) : storage_bytes(e.storage);
+    const size_t es = reduce_out ? reduce_bytes(e.storage) : storage_bytes(slot_dtype(e, k));
     const size_t width = size_t(b.rows) * es, pitch = size_t(b.ld) * es;
     if (b.rows * b.cols == 0) continue;
     if (k < e.n_in) {

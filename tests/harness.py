@@ -38,6 +38,7 @@ TREES = {
     "swish": "(/ X (+ 1 (exp (neg (* {s0} X)))))",
     "gelu": "(% (/ X 2) (+ 1 (tanh (* {s0} (+ X (* {s1} (pow X 3)))))))",
     "sum_schur": "(% (+ A B) (+ C D))",
+    "expr3": "(/ 1 (+ (% X (f32 Y)) (log (% (log (+ X 2)) W))))",
     # matrix products (Fig. 1, a product with an element-wise remainder, Sec. 4 chain)
     "gemm_scale": "(* {s0} (* X (t Y)))",
     "gemm_epilogue": "(sigmoid (+ (* {s0} (* X Y)) W))",
@@ -64,6 +65,7 @@ SLOTS = {
     "expr1": ["X", "Y"], "expr2": ["A", "B", "C", "D"], "relu": ["X"], "sigmoid": ["X"],
     "swish": ["X"], "gelu": ["X"], "sum_schur": ["A", "B", "C", "D"],
     "gemm_scale": ["X", "Y"], "gemm_epilogue": ["X", "Y", "W"], "chain": ["A", "B", "C", "D"],
+    "expr3": ["X", "Y", "W"],
 }
 for _n in range(2, 17):
     SLOTS[f"add{_n}"] = [f"A{_k}" for _k in range(1, _n + 1)]
@@ -76,7 +78,7 @@ TOL_TRANS = {"f64": 1e-13, "f32": 1e-5, "bf16": 8e-3, "f16": 1e-3}
 # compensated FP32 accumulation, so they are held to the FP32 reduction bound
 TOL_RED = {"f64": 1e-13, "f32": 1e-5, "bf16": 1e-5, "f16": 1e-5}
 HAS_TRANSCENDENTAL = {"schur_exp_trans", "schur_sqrt_sigmoid", "sigmoid_sqloss", "expr2",
-                      "sigmoid", "swish", "gelu", "gemm_epilogue"}
+                      "sigmoid", "swish", "gelu", "gemm_epilogue", "expr3"}
 
 
 def tree_of(name, scalars=None):

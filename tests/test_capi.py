@@ -137,3 +137,35 @@ def test_status_strings(fxlib):
     for s in range(0, -10, -1):
         assert fxlib.fx_status_string(s)
     fxlib.fx_expr_destroy(None)
+
+
+def test_slot_dtypes(fxlib):
+    h = fxlib.fx_expr_create("expr3", fxlib.FX_F32)
+    try:
+        assert [fxlib.fx_expr_slot_dtype(h, k) for k in range(4)] == [
+            fxlib.FX_F32, fxlib.FX_F64, fxlib.FX_F32, fxlib.FX_F32]
+        # the FP64 slot wants 8-byte alignment
+        with pytest.raises(fxlib.FxError) as e:
+            fxlib.fx_expr_bind(h, 1, 0x1004, 8, 6, 8)
+        assert e.value.status == -4
+        fxlib.fx_expr_bind(h, 0, 0x1004, 8, 6, 8)
+    finally:
+        fxlib.fx_expr_destroy(h)
+    h = fxlib.fx_expr_create("sqdiff_accu", fxlib.FX_BF16)
+    try:
+        assert fxlib.fx_expr_slot_dtype(h, 0) == fxlib.FX_BF16
+        assert fxlib.fx_expr_slot_dtype(h, 2) == fxlib.FX_F32      # the accu output
+        with pytest.raises(fxlib.FxError):
+            fxlib.fx_expr_slot_dtype(h, 3)
+    finally:
+        fxlib.fx_expr_destroy(h)
+
+
+def test_product_trees_listed(fxlib):
+    h = fxlib.fx_expr_create("gemm_scale", fxlib.FX_BF16)
+    try:
+        assert fxlib.fx_expr_info(h)[:2] == (2, 1)
+    finally:
+        fxlib.fx_expr_destroy(h)
+    h = fxlib.fx_expr_create("chain", fxlib.FX_F32)
+    fxlib.fx_expr_destroy(h)

@@ -395,6 +395,19 @@ def test_sigma_bounds_float32_matrix_products(tree):
     assert np.all(s > 0)
 
 
+def test_f32_conversion():
+    """conv_to<fmat> (Sec. 4 expr3): round to nearest even into FP32."""
+    vals = np.array([0.1, 1.0 + 2.0 ** -30, 1.0 + 3 * 2.0 ** -24, 2.0 ** 128, -2.5, 1e-46])
+    env = {"Y": synth.Buffer(vals, 6, 1, 6, "f64")}
+    got = oracle.evaluate("(f32 Y)", env)[:, 0]
+    assert got[0] == 0.100000001490116119384765625          # nearest FP32 to 0.1
+    assert got[1] == 1.0                                       # below half an ulp
+    assert got[2] == 1.0 + 4 * 2.0 ** -24                      # tie at 1.5 ulp -> even (2 ulp)
+    assert np.isinf(got[3]) and got[4] == -2.5 and got[5] == 0.0
+    envf = synth.operands(5, [("X", 7, 3)], "f32", "normal")
+    assert np.array_equal(oracle.evaluate("(f32 X)", envf), oracle.evaluate("X", envf))
+
+
 def test_matrix_product_closed_forms():
     """ones(n, k) * ones(k, m) = k everywhere, with sigma = k * k; (A B)^T =
     B^T A^T exactly in FP64 for small integers."""

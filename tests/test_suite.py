@@ -63,6 +63,28 @@ def test_suite_expressions(fx, name):
         check(name, got, env, f" at {R}x{C}")
 
 
+def expr3_env(seed, R, C):
+    """expr3's inputs: X and W positive FP32 (the logs stay defined), Y FP64."""
+    env = synth.operands(seed, [("X", R, C), ("W", R, C)], "f32", "positive")
+    env.update(synth.operands(seed + 1, [("Y", R, C)], "f64", "normal"))
+    return env
+
+
+def test_expr3_mixed_storage(fx):
+    """Sec. 4 expr3: an FP64 leaf in an FP32 tree, read as its FP32 rounding."""
+    h = fx.fx_expr_create("expr3", fx.FX_F32)
+    try:
+        assert [fx.fx_expr_slot_dtype(h, k) for k in range(4)] == [fx.FX_F32, fx.FX_F64, fx.FX_F32,
+                                                                   fx.FX_F32]
+    finally:
+        fx.fx_expr_destroy(h)
+    for R, C in SHAPES + [(1000, 700)]:
+        env = expr3_env(110, R, C)
+        got = run(fx, "expr3", "f32", env, R, C)
+        check("expr3", got, env, f" at {R}x{C}")
+        assert got["_launches"] == 1
+
+
 def _submatrix(parent, r0, c0, rows, cols):
     """A view of `parent` (a synth.Buffer): pointer offset, the parent's ld."""
     off = r0 + c0 * parent.ld
