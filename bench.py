@@ -50,7 +50,12 @@ METRIC = "fused-expr effective HBM GB/s (% of GB300 peak) and speedup vs unfused
 
 # DRAM traffic per launch of a dominant kernel from an ncu capture (bytes),
 # valid only while the kernel sources hash to the recorded value.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first
+    # timed launch of Z at 8192^2 FP32 (profiles/k_flat_schur_sqrt_sigmoid_f32.md):
+    # 1,073,779,456 read + 215,429,632 written (the rest of Z still in L2)
+    ("expr8192", "Z"): {"bytes": 1073779456 + 215429632, "hash": "72571fe488c04e3e"},
+}
 
 # FP64-pipe instructions per output element of FP64 trees (per lane: DFMA,
 # DADD and DMUL each take one slot), counted with ncu
@@ -378,6 +383,22 @@ def cpu_oracle_time(R, cols, storage):
     return time.perf_counter() - t0, nbytes
 
 
+def _oracle_worker(a):
+    R, cols, storage = a
+    return cpu_oracle_time(R, cols, storage)
+
+
+def cpu_oracle_time_all_cores(R, cols, storage, nproc):
+    """The same oracle on nproc panels at once, one process per core
+    (spawned, so no CUDA state is inherited): (wall s of the slowest, bytes)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(nproc) as pool:
+        pool.map(_oracle_worker, [(R, 8, storage)] * nproc)      # imports and warm-up
+        res = pool.map(_oracle_worker, [(R, cols, storage)] * nproc)
+    return max(t for t, _ in res), sum(b for _, b in res)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -512,13 +533,20 @@ def run_ours(args, rank, world):
     z_gbs = dom_op.bytes / (per_ms[dom] / 1e3) / 1e9
     tr = TRAFFIC.get((args.workload, dom))
     traffic = tr["bytes"] if tr and tr["hash"] == kernel_source_hash() else None
-    cpu = None
+    cpu = cpu_all = None
     if world == 1 and args.workload == "expr8192" and args.size == 8192 and not args.no_cpu:
         t_cpu, b_cpu = cpu_oracle_time(8192, args.cpu_cols, "f32")
         cpu = {"value": round(b_cpu / t_cpu / 1e9, 4), "unit": "GB/s", "cores": 1,
                "kind": "oracle",
                "sample": f"8192x{args.cpu_cols} column panel of X,Y,W,V, all four trees, "
                          "FP64 numpy tree walker, one thread"}
+        ncores = os.cpu_count() or 1
+        if ncores > 1:
+            t_par, b_par = cpu_oracle_time_all_cores(8192, max(1, args.cpu_cols // 4), "f32", ncores)
+            cpu_all = {"value": round(b_par / t_par / 1e9, 4), "unit": "GB/s", "cores": ncores,
+                       "kind": "oracle",
+                       "sample": f"{ncores} processes, each an 8192x{max(1, args.cpu_cols // 4)} "
+                                 "panel, all four trees; bytes of all panels over the slowest"}
     cfg["parallelism"] = f"replicas x{world}"
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
@@ -542,6 +570,8 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if cpu_all:
+        line["cpu_baseline_all_cores"] = cpu_all
     if (args.workload, dom) in FP64_PIPE_OPS:
         alu = fp64_roofline(fx, sp, args.workload, dom, dom_op, per_ms[dom], peak, storage, cfg)
         if alu:

@@ -99,9 +99,12 @@ FX_D IssueDesc<NIN> fetch_item(const BatchMat* mats, const BatchItem* items, int
   d.ldz = KIND != FX_KIND_FULL_REDUCE ? m.ld[NIN] : 0;
   d.R = m.rows;
   d.C = m.cols;
-  const int64_t tiles_r = (d.R + TR - 1) / TR;
-  d.r0 = (w.tile % tiles_r) * TR;
-  d.c0 = (w.tile / tiles_r) * TC;
+  // 32-bit: a batch matrix has fewer than 2^31 tiles (64-bit division is a
+  // long instruction sequence, executed here by every thread for every item)
+  const uint32_t tiles_r = uint32_t((d.R + TR - 1) / TR);
+  const uint32_t tc = uint32_t(w.tile) / tiles_r;
+  d.r0 = int64_t(uint32_t(w.tile) - tc * tiles_r) * TR;
+  d.c0 = int64_t(tc) * TC;
   d.item = it;
   d.mat = w.mat;
   d.vec = m.vec;
