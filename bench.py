@@ -402,7 +402,13 @@ def cpu_oracle_time_all_cores(R, cols, storage, nproc):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    R, cols = 8192, args.ref_cols
+    R = 8192
+    # the sample per step is sized so that warm-up and timed steps together
+    # take about 100 s of CPU time (at most --ref-cols columns per step)
+    t64, _ = cpu_oracle_time(R, 64, "f32")
+    per_col = max(t64 / 64, 1e-6)
+    budget = 100.0 / max(1, args.steps + args.warmup)
+    cols = int(max(8, min(args.ref_cols, budget / per_col)))
     for _ in range(args.warmup):
         cpu_oracle_time(R, cols, "f32")
     tt, tb = 0.0, 0
