@@ -1,6 +1,6 @@
 """Benchmark of fused expression evaluation on one GB300 (or N replicas).
 
-Default workload (the JSON line the driver reads): one step evaluates, on
+Default workload (the JSON line printed with no flags): one step evaluates, on
 four 8192 x 8192 column-major FP32 matrices X, Y, W, V drawn i.i.d. N(0, 1)
 (seed 1),
     Z      = X % Y + sqrt(abs(W)) / (1 + exp(-V))

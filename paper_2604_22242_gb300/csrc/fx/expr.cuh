@@ -47,6 +47,10 @@ FX_D float m_abs(float x) { return ::fabsf(x); }
 FX_D double m_abs(double x) { return ::fabs(x); }
 FX_D float m_tanh(float x) { return ::tanhf(x); }
 FX_D double m_tanh(double x) { return ::tanh(x); }
+// 1 / x correctly rounded (the same value as the IEEE division 1 / x,
+// without the general division's numerator handling)
+FX_D float m_rcp(float x) { return __frcp_rn(x); }
+FX_D double m_rcp(double x) { return __drcp_rn(x); }
 FX_D float m_pow(float x, float k) { return ::powf(x, k); }
 FX_D double m_pow(double x, double k) { return ::pow(x, k); }
 template <class C> FX_D C m_sign(C x) { return x > C(0) ? C(1) : (x < C(0) ? C(-1) : C(0)); }
@@ -66,7 +70,7 @@ struct OpMul {
 struct OpDiv {
   template <class C> static FX_D C f(C a, C b) { return a / b; }
   template <class C> static FX_D void d(C a, C b, C& da, C& db) {
-    da = C(1) / b;
+    da = m_rcp(b);
     db = -a / (b * b);
   }
 };
@@ -111,7 +115,7 @@ struct OpSquare {
   template <class C> static FX_D C d(C a, C) { return C(2) * a; }
 };
 struct OpSigmoid {  // Sec. 4: sigmoid = 1 / (1 + exp(-X))
-  template <class C> static FX_D C f(C a) { return C(1) / (C(1) + m_exp(-a)); }
+  template <class C> static FX_D C f(C a) { return m_rcp(C(1) + m_exp(-a)); }
   template <class C> static FX_D C d(C, C z) { return z * (C(1) - z); }
 };
 struct OpTanh {

@@ -168,6 +168,20 @@ FX_D void load_rc(Pack<LL, V, CT>& p, const Slots& sl, int64_t r, int64_t c, int
 // put(state, off, v, nvalid): lanes 0..nvalid-1 of v are the tree's values
 // at output offset off .. off+nvalid-1 (off = r + c*ldz).
 
+// Pairwise sum of a vector's V lanes (V a power of two): one compensated
+// add per vector instead of one per lane; the tree adds log2(V) roundings
+// per element to a sum that is then accumulated compensated.
+template <class CT, int V> FX_D CT lane_sum(const CT (&v)[V]) {
+  if constexpr (V == 1) {
+    return v[0];
+  } else {
+    CT h[V / 2];
+#pragma unroll
+    for (int j = 0; j < V / 2; ++j) h[j] = v[2 * j] + v[2 * j + 1];
+    return lane_sum<CT, V / 2>(h);
+  }
+}
+
 template <class T, int V> struct EpiStore {
   T* z;
   int64_t ldz;
@@ -199,9 +213,16 @@ template <class CTy, int V, bool SQ> struct EpiSum {
   static constexpr bool sqrt_result = SQ;
   using State = ThreadSum<CTy>;
   template <class CT> FX_D void put(State& st, int64_t, const CT (&v)[V], int nvalid) const {
+    if (nvalid == V) {
+      CT w[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j)
-      if (j < nvalid) st.add(SQ ? v[j] * v[j] : v[j]);
+      for (int j = 0; j < V; ++j) w[j] = SQ ? v[j] * v[j] : v[j];
+      st.add(lane_sum(w));
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid) st.add(SQ ? v[j] * v[j] : v[j]);
+    }
   }
 };
 
@@ -217,9 +238,13 @@ template <class T, int V> struct EpiStoreSum {
     EpiStore<T, V> s{z, ldz};
     typename EpiStore<T, V>::State d;
     s.put(d, off, v, nvalid);
+    if (nvalid == V) {
+      st.add(lane_sum(v));
+    } else {
 #pragma unroll
-    for (int j = 0; j < V; ++j)
-      if (j < nvalid) st.add(v[j]);
+      for (int j = 0; j < V; ++j)
+        if (j < nvalid) st.add(v[j]);
+    }
   }
 };
 
@@ -576,11 +601,15 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
           if (nv > 0) {
             CT v[V];
             eval_lanes<V>(e, p[u], v);
+            if (!ISMAX && nv == V) {
+              acc.add(lane_sum(v));
+            } else {
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-              if (j < nv) {
-                if (ISMAX) m = max_nan(m, v[j]);
-                else acc.add(v[j]);
+              for (int j = 0; j < V; ++j) {
+                if (j < nv) {
+                  if (ISMAX) m = max_nan(m, v[j]);
+                  else acc.add(v[j]);
+                }
               }
             }
           }

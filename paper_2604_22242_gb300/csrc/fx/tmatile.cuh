@@ -283,9 +283,16 @@ __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl
           *reinterpret_cast<Raw<T, V>*>(zt + (r / G::IB) * G::BOX + swz<G::es>(r % G::IB, c)) = o;
         }
         if constexpr (Epi::reduces) {
+          if (nvalid == V) {
+            CT w[V];
 #pragma unroll
-          for (int j = 0; j < V; ++j)
-            if (j < nvalid) st.add(Epi::sqrt_result ? v[j] * v[j] : v[j]);
+            for (int j = 0; j < V; ++j) w[j] = Epi::sqrt_result ? v[j] * v[j] : v[j];
+            st.add(lane_sum(w));
+          } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+              if (j < nvalid) st.add(Epi::sqrt_result ? v[j] * v[j] : v[j]);
+          }
         }
       }
       tma::arrive(&ring.empty[s]);
@@ -310,7 +317,7 @@ __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl
 
 // ---------------------------------------------------------------- host side
 
-// cuTensorMapEncodeTiled from the driver, found once through the runtime.
+// cuTensorMapEncodeTiled from the CUDA driver, found once through the runtime.
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
