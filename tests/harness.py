@@ -148,10 +148,12 @@ def check_canary(t, start, guard=64):
 
 
 def run(fx, name, storage, env, R, C, ldz=None, offset=0, unfused=False, scalars=None,
-        stream=None, shape=None):
+        stream=None, shape=None, tune=None):
     """Evaluates `name` on device copies of `env`; returns the outputs as FP64.
 
-    shape: (block, unroll, blocks_per_sm, pipeline) to fix the launch shape."""
+    shape: (block, unroll, blocks_per_sm, pipeline) to fix the launch shape;
+    tune: "search" or "cache" to run the autotuner on the bound buffers first
+    (the chosen shape is returned under "_shape")."""
     import torch
     h = fx.fx_expr_create(name, STORAGE_CODE[storage])
     try:
@@ -191,6 +193,8 @@ def run(fx, name, storage, env, R, C, ldz=None, offset=0, unfused=False, scalars
                 fx.fx_expr_bind(h, n_in, v.data_ptr(), R, 1, max(R, 1))
             outs["v"] = (v, "v")
         sp = 0 if stream is None else stream
+        if tune is not None:
+            fx.fx_tune(h, tune, sp)
         if unfused:
             fx.fx_eval_unfused(h, sp)
         else:
@@ -217,6 +221,7 @@ def run(fx, name, storage, env, R, C, ldz=None, offset=0, unfused=False, scalars
                 check_canary(t, nv)
                 result["v"] = from_device(t[:nv], "f64")
         result["_launches"] = launches
+        result["_shape"] = tuple(fx.fx_expr_launch_shape(h))
         return result
     finally:
         fx.fx_expr_destroy(h)
