@@ -459,6 +459,12 @@ def run_ours(args, rank, world):
     if args.tune:
         for h in handles:
             fx.fx_tune(h, "search", sp)
+    if "batch" in keep:
+        # the batched workload is autotuned (block size, stages, residency)
+        hb, items = keep["batch"][6], keep["batch"][5]
+        fx.fx_tune_batch(hb, items, "search", sp)
+        cfg["launch_shape"] = "autotuned: block %d, unroll %d, blocks/SM %d, pipeline %d" % tuple(
+            fx.fx_expr_launch_shape(hb))
     flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
     torch.cuda.synchronize()
     step_bytes = sum(o.bytes for o in ops)

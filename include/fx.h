@@ -193,6 +193,16 @@ fx_status fx_eval_backward(fx_expr* x, const void* grad_out, void* const* grad_p
  * ($FX_TUNE_CACHE, default ./fx_tune.json). */
 fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream);
 
+/* Autotuner of the batched entry (fx_eval_batch): times the batched
+ * kernel's launch shapes - threads per block 256 or 512 (512 not for BF16 /
+ * FP16), 2, 3 or 4 pipeline stages (reported as unroll 2, 4, 8), blocks per
+ * SM 0 (as many as fit), 1 or 2 - on the given items without graph capture,
+ * keeps the fastest and caches it under (expression, storage, device, n).
+ * FX_TUNE_CACHE reads the cache; FX_TUNE_OFF restores the defaults. The
+ * next fx_eval_batch uses the chosen shape (and re-captures its graph). */
+fx_status fx_tune_batch(fx_expr* x, int64_t n, const fx_batch_item* items, fx_tune_mode mode,
+                        void* stream);
+
 /* Launch shape currently chosen (for reports): threads per block, vectors
  * per thread per step, blocks per SM (0: as many as fit), and the kernel
  * variant (see fx_expr_set_launch_shape). Null pointers are skipped. */

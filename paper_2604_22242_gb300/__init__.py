@@ -20,7 +20,7 @@ __all__ = [
     "fx_expr_bind", "fx_expr_set_scalar", "fx_expr_get_scalar", "fx_eval", "fx_eval_unfused",
     "fx_eval_host", "fx_eval_batch", "fx_eval_backward", "fx_tune", "fx_expr_launch_shape",
     "fx_expr_set_launch_shape", "fx_fp64_fma_rate", "fx_expr_slot_dtype",
-    "fx_selftest_wait_timeout",
+    "fx_selftest_wait_timeout", "fx_tune_batch",
     "fx_expr_last_launches", "fx_expr_sync_status", "fx_last_error_string", "fx_status_string", "BatchItem",
     "colmajor", "bind_tensor", "Expr", "FusedLoss", "DTYPE_OF",
 ]
@@ -84,6 +84,7 @@ def lib():
         "fx_fp64_fma_rate": (st, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fx_expr_slot_dtype": (st, [vp, i32, ctypes.POINTER(i32)]),
         "fx_selftest_wait_timeout": (st, [vp, ctypes.POINTER(ctypes.c_uint)]),
+        "fx_tune_batch": (st, [vp, i64, ctypes.POINTER(BatchItem), i32, vp]),
         "fx_expr_last_launches": (i32, [vp]),
         "fx_expr_sync_status": (st, [vp, vp]),
         "fx_last_error_string": (ctypes.c_char_p, []),
@@ -183,6 +184,11 @@ def fx_eval_backward(h, grad_out_ptr, grad_ptrs, stream: int = 0):
 
 def fx_tune(h, mode: str = "search", stream: int = 0):
     _check(lib().fx_tune(h, TUNE[mode], stream or None))
+
+
+def fx_tune_batch(h, items, mode: str = "search", stream: int = 0):
+    """items: a ctypes array of BatchItem (as for fx_eval_batch)."""
+    _check(lib().fx_tune_batch(h, len(items), items, TUNE[mode], stream or None))
 
 
 def fx_expr_launch_shape(h):

@@ -312,6 +312,7 @@ struct BatchCacheEntry {
   double2* part = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t exec_stream = nullptr;
+  int exec_shape[3] = {0, 0, 0};  // launch shape the graph was captured with
 };
 
 }  // namespace fx
@@ -386,7 +387,8 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
   using CT = ct_of<E>;
   constexpr int V = vec_width<E, 16>();
   constexpr bool dbl = std::is_same<CT, double>::value;
-  constexpr int TR = dbl ? 32 : 64, TCc = 32, NT = 256, NBUF = 3;
+  constexpr int TR = dbl ? 32 : 64, TCc = 32;
+  constexpr int NTMAX = 512;  // partials are sized for the largest block
   const int n_in = NIN;
   if constexpr (root_of<Root>::kind == FX_KIND_DIM_REDUCE) {
     return fail(FX_E_UNSUPPORTED, "batched dim reductions are not fused");
@@ -458,7 +460,7 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
       }
       const size_t bm = ((sizeof(BatchMat) * n) + 255) & ~size_t(255);
       const size_t bi = ((sizeof(BatchItem) * work.size()) + 255) & ~size_t(255);
-      const size_t bp = sizeof(double2) * (NT / 32) * (work.size() > 0 ? work.size() : 1);
+      const size_t bp = sizeof(double2) * (NTMAX / 32) * (work.size() > 0 ? work.size() : 1);
       FX_TRY(c.dev.ensure(bm + bi + bp, st));
       char* base = static_cast<char*>(c.dev.p);
       c.mats = reinterpret_cast<BatchMat*>(base);
@@ -474,29 +476,56 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
     }
     const E& e = inner_of(root);
     Run r = run_of(x, st);
+    // Launch shape (tunable, fx_tune_batch): threads per block 256 or 512
+    // (512 not for 2-byte types), 2, 3 or 4 pipeline stages (unroll 2, 4,
+    // 8), blocks per SM (0: as many as fit).
+    const int NTsel = (r.tune.block >= 512 && sizeof(T) != 2) ? 512 : 256;
+    const int NBsel = r.tune.unroll <= 2 ? 2 : (r.tune.unroll >= 8 ? 4 : 3);
+    auto launch_one = [&](auto nt_c, auto nb_c) -> fx_status {
+      constexpr int NT = decltype(nt_c)::value, NBUF = decltype(nb_c)::value;
+      constexpr int KE = kind == FX_KIND_MULTI ? FX_KIND_MULTI : KIND0;
+      auto kern = k_batch_async<E, T, TR, TCc, NT, NBUF, KE, NIN>;
+      constexpr int smem = NBUF * abuf_bytes<LL, TR, TCc>() + NBUF * int(sizeof(TileDesc));
+      FX_TRY(allow_smem(kern, smem));
+      const int sms = device_sms() > 0 ? device_sms() : 1;
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+      }
+      const int bps = r.tune.bps > 0 ? (r.tune.bps < occ ? r.tune.bps : occ) : occ;
+      int64_t grid = int64_t(sms) * bps;
+      if (grid > c.nitems) grid = c.nitems;
+      kern<<<unsigned(grid), NT, smem, st>>>(e, c.mats, c.items, c.nitems, c.part);
+      return after_launch(r, "k_batch_async");
+    };
+    using I256 = std::integral_constant<int, 256>;
+    using I512 = std::integral_constant<int, (sizeof(T) == 2 ? 256 : 512)>;
+    using B2 = std::integral_constant<int, 2>;
+    using B3 = std::integral_constant<int, 3>;
+    using B4 = std::integral_constant<int, 4>;
     auto launch_all = [&]() -> fx_status {
       if (c.nitems > 0) {
-        constexpr int KE = kind == FX_KIND_MULTI ? FX_KIND_MULTI : KIND0;
-        auto kern = k_batch_async<E, T, TR, TCc, NT, NBUF, KE, NIN>;
-        constexpr int smem = NBUF * abuf_bytes<LL, TR, TCc>() + NBUF * int(sizeof(TileDesc));
-        FX_TRY(allow_smem(kern, smem));
-        const int sms = device_sms() > 0 ? device_sms() : 1;
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess || occ < 1) occ = 1;
-        const int bps = r.tune.bps > 0 ? (r.tune.bps < occ ? r.tune.bps : occ) : occ;
-        int64_t grid = int64_t(sms) * bps;
-        if (grid > c.nitems) grid = c.nitems;
-        kern<<<unsigned(grid), NT, smem, st>>>(e, c.mats, c.items, c.nitems, c.part);
-        FX_TRY(after_launch(r, "k_batch_async"));
+        if (NTsel == 512) {
+          if (NBsel == 2) FX_TRY(launch_one(I512{}, B2{}));
+          else if (NBsel == 4) FX_TRY(launch_one(I512{}, B4{}));
+          else FX_TRY(launch_one(I512{}, B3{}));
+        } else {
+          if (NBsel == 2) FX_TRY(launch_one(I256{}, B2{}));
+          else if (NBsel == 4) FX_TRY(launch_one(I256{}, B4{}));
+          else FX_TRY(launch_one(I256{}, B3{}));
+        }
       }
       if (has_s && c.n > 0) {
-        k_batch_combine<CT><<<unsigned((c.n + 7) / 8), 256, 0, st>>>(c.mats, c.n, c.part, sslot, NT / 32);
+        k_batch_combine<CT><<<unsigned((c.n + 7) / 8), 256, 0, st>>>(c.mats, c.n, c.part, sslot,
+                                                                     NTsel / 32);
         FX_TRY(after_launch(r, "k_batch_combine"));
       }
       return FX_OK;
     };
     if (!use_graph || st == nullptr) return launch_all();
-    if (!c.exec || c.exec_stream != st) {
+    const int shape[3] = {NTsel, NBsel, r.tune.bps};
+    if (!c.exec || c.exec_stream != st || memcmp(shape, c.exec_shape, sizeof shape) != 0) {
       if (c.exec) {
         cudaGraphExecDestroy(c.exec);
         c.exec = nullptr;
@@ -515,6 +544,7 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
       cudaGraphDestroy(g);
       if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
       c.exec_stream = st;
+      memcpy(c.exec_shape, shape, sizeof shape);
       x->last_launches = before;
     }
     FX_CUDA(cudaGraphLaunch(c.exec, st));

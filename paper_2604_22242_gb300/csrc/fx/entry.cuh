@@ -105,6 +105,56 @@ template <class LL, bool ALL_MIXED = false> struct SlotModes {
   }
 };
 
+// Batch autotuner: the same search over the batched kernel's launch shapes
+// (threads per block 256 / 512, 2 / 3 / 4 stages, blocks per SM), timed on
+// the given items without graph capture; cached under the batch size.
+using BatchRunFn = fx_status (*)(fx_expr*, int64_t, const fx_batch_item*, cudaStream_t, int);
+inline fx_status run_tune_batch(fx_expr* x, int mode, cudaStream_t st, int64_t n,
+                                const fx_batch_item* items, BatchRunFn run) {
+  const std::string key = "batch|" + tune_key(x) + "|" + std::to_string(n);
+  if (mode == FX_TUNE_CACHE) {
+    Tune t;
+    if (tune_cache_get(key, t)) x->tune = t;
+    return FX_OK;
+  }
+  static const int blocks[] = {256, 512};
+  static const int unrolls[] = {2, 4, 8};
+  static const int bpss[] = {0, 1, 2};
+  cudaEvent_t a, b;
+  FX_CUDA(cudaEventCreate(&a));
+  FX_CUDA(cudaEventCreate(&b));
+  Tune best{};
+  float best_ms = 1e30f;
+  fx_status status = FX_OK;
+  for (int bl : blocks)
+    for (int un : unrolls)
+      for (int bp : bpss) {
+        x->tune = Tune{bl, un, bp, true, 0};
+        for (int w = 0; w < 2 && status == FX_OK; ++w) status = run(x, n, items, st, 0);
+        if (status != FX_OK) break;
+        cudaEventRecord(a, st);
+        for (int it = 0; it < 3 && status == FX_OK; ++it) status = run(x, n, items, st, 0);
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) status = cuda_fail(cudaGetLastError(), "tune");
+        if (status != FX_OK) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = x->tune;
+        }
+      }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (status != FX_OK) {
+    x->tune = Tune{};
+    return status;
+  }
+  x->tune = best;
+  tune_cache_put(key, best);
+  return FX_OK;
+}
+
 template <class Def, class T> struct Inst {
   static auto root(const fx_expr* x) { return normalize(Def::template build<T>(x->scal)); }
   using Root = std::decay_t<decltype(normalize(Def::template build<T>(nullptr)))>;
@@ -130,6 +180,11 @@ template <class Def, class T> struct Inst {
   static fx_status tune(fx_expr* x, int mode, cudaStream_t st) {
     return run_tune(x, mode, st, &eval, 3);
   }
+  static fx_status tune_batch(fx_expr* x, int mode, cudaStream_t st, int64_t n,
+                              const fx_batch_item* items) {
+    if constexpr (Def::batchable && !prods) return run_tune_batch(x, mode, st, n, items, &batch);
+    else return fail(FX_E_UNSUPPORTED, "no batched entry");
+  }
   // input slots of trees with products are consumed by GEMMs: mode -1
   // (no column-chunked host pipeline)
   static constexpr SlotModes<leaves_t<typename root_of<typename Lift<Root, T, Def::n_in>::type>::inner>,
@@ -138,7 +193,7 @@ template <class Def, class T> struct Inst {
     return Entry{Def::name, Def::formula, dtype_of<T>::value, Def::n_in, Def::n_out, Def::n_scal,
                  fx_kind(Def::kind), Def::slots, Def::defaults, &eval, &unfused,
                  Def::batchable ? &batch : nullptr, Def::differentiable ? &backward : nullptr,
-                 &tune, modes.m, modes.dt};
+                 &tune, modes.m, modes.dt, Def::batchable && !prods ? &tune_batch : nullptr};
   }
 };
 

@@ -92,6 +92,8 @@ struct Entry {
   const signed char* slot_modes;
   // storage type of each input slot (-1: the entry's storage type)
   const signed char* slot_dtypes;
+  // autotuner of the batched entry (null when there is none)
+  fx_status (*tune_batch)(fx_expr*, int, cudaStream_t, int64_t, const fx_batch_item*);
 };
 
 // Storage type of slot k of an entry (outputs: the entry's storage type;

@@ -507,6 +507,19 @@ fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream) {
   return x->e->tune(x, int(mode), static_cast<cudaStream_t>(stream));
 }
 
+fx_status fx_tune_batch(fx_expr* x, int64_t n, const fx_batch_item* items, fx_tune_mode mode,
+                        void* stream) {
+  if (!x) return fail(FX_E_ARG, "null expression");
+  if (mode < FX_TUNE_OFF || mode > FX_TUNE_SEARCH) return fail(FX_E_ARG, "bad tune mode");
+  if (!x->e->tune_batch) return fail(FX_E_UNSUPPORTED, "'%s' has no batched entry", x->e->name);
+  if (n < 0 || (n > 0 && !items)) return fail(FX_E_ARG, "bad batch");
+  if (mode == FX_TUNE_OFF) {
+    x->tune = Tune{};
+    return FX_OK;
+  }
+  return x->e->tune_batch(x, int(mode), static_cast<cudaStream_t>(stream), n, items);
+}
+
 fx_status fx_expr_launch_shape(const fx_expr* x, int* block, int* unroll, int* bps,
                                int* pipeline) {
   if (!x) return fail(FX_E_ARG, "null expression");

@@ -33,7 +33,8 @@ def arena(mats, dtype, align=4):
     return torch.from_numpy(host).cuda(), offs
 
 
-def run_batch(fx, rows, cols, ops, use_graph, repeat=1, storage=0):
+def run_batch(fx, rows, cols, ops, use_graph, repeat=1, storage=0, shape=None, tune=None,
+              shape_out=None):
     import torch
     n = len(rows)
     A, oa = arena(ops["A"], None)
@@ -57,6 +58,12 @@ def run_batch(fx, rows, cols, ops, use_graph, repeat=1, storage=0):
     h = fx.fx_expr_create("schur_trans_accu", storage)
     stream = torch.cuda.Stream()
     try:
+        if shape is not None:
+            fx.fx_expr_set_launch_shape(h, *shape)
+        if tune is not None:
+            fx.fx_tune_batch(h, items, tune, int(stream.cuda_stream))
+        if shape_out is not None:
+            shape_out.append(tuple(fx.fx_expr_launch_shape(h)))
         for _ in range(repeat):
             fx.fx_eval_batch(h, items, int(stream.cuda_stream), use_graph)
         stream.synchronize()
@@ -110,3 +117,28 @@ def test_batch_4096_log_uniform(fx):
                    {int(np.argmax(rows * cols)), int(np.argmin(rows * cols))})
     check(ops, rows, cols, zs, ss, which)
     assert np.all(np.isfinite(ss))
+
+
+@pytest.mark.parametrize("shape", [(512, 2, 0, 0), (256, 8, 1, 0), (512, 4, 2, 0), (256, 2, 0, 0)])
+def test_batch_launch_shapes(fx, shape):
+    """Every batched launch shape the tuner picks from: 256/512 threads,
+    2/3/4 stages, residency; direct and graph-captured."""
+    rows, cols, ops = synth.batch_operands(7, 50, [("A", False), ("B", False), ("C", True)],
+                                           lo=1, hi=260)
+    for use_graph in (False, True):
+        zs, ss, _ = run_batch(fx, rows, cols, ops, use_graph, repeat=2, shape=shape)
+        check(ops, rows, cols, zs, ss, range(len(rows)))
+
+
+def test_batch_autotune(fx, tmp_path, monkeypatch):
+    monkeypatch.setenv("FX_TUNE_CACHE", str(tmp_path / "tune.json"))
+    rows, cols, ops = synth.batch_operands(8, 64, [("A", False), ("B", False), ("C", True)],
+                                           lo=16, hi=400)
+    got = []
+    zs, ss, _ = run_batch(fx, rows, cols, ops, True, tune="search", shape_out=got)
+    check(ops, rows, cols, zs, ss, range(len(rows)))
+    b, u, s, p = got[0]
+    assert b in (256, 512) and u in (2, 4, 8) and s in (0, 1, 2)
+    again = []
+    run_batch(fx, rows, cols, ops, True, tune="cache", shape_out=again)
+    assert again[0] == got[0]
