@@ -27,6 +27,11 @@ struct BatchMat {
   int64_t first;   // first work item of this matrix
   int32_t ntiles;
   int32_t vec;     // every full vector of this matrix is aligned
+  // skewed tiles: every plain leaf and Z share one leading dimension and one
+  // base alignment, so shifting each column's rows by its misalignment
+  // (sbase + col * ld) mod W makes all their 16-byte chunks aligned
+  int32_t skew;
+  int32_t sbase;   // (first plain leaf's address / element size) mod W
 };
 struct BatchItem {
   int32_t mat;
@@ -53,19 +58,24 @@ struct TileDesc {
   int64_t ldz;
   int64_t R, C, r0, c0;
   int64_t item;
+  int64_t sld;     // leading dimension the skew follows (0: no skew)
   int32_t mat;
   int32_t valid;
+  int32_t sbase;
 };
 
 // Shared-memory layout of one buffer: plain leaves TC columns of TR rows,
-// transposed leaves TR rows of TC+1 elements.
+// transposed leaves TR + W - 1 rows (the rows any column's skew can reach,
+// W = 16 / element size) of TC+1 elements.
 template <class LL, int TR, int TC, int I = 0> FX_HD constexpr int abuf_offset() {
   if constexpr (I == 0) {
     return 0;
   } else {
     using L = typename tl_at<LL, I - 1>::type;
     constexpr int es = int(sizeof(typename L::elem));
-    constexpr int sz = L::mode == MN ? TR * TC * es : (L::mode == MT ? TR * (TC + 1) * es : 0);
+    constexpr int W = 16 / es;
+    constexpr int sz = L::mode == MN ? TR * TC * es
+                                     : (L::mode == MT ? (TR + W - 1) * (TC + 1) * es : 0);
     return abuf_offset<LL, TR, TC, I - 1>() + ((sz + 15) / 16) * 16;
   }
 }
@@ -78,11 +88,16 @@ template <int NIN> struct IssueDesc {
   const void* p[NIN];
   int64_t ld[NIN];
   const void* z;
-  int64_t ldz, R, C, r0, c0, item;
-  int32_t mat, vec, valid;
+  int64_t ldz, R, C, r0, c0, item, sld;
+  int32_t mat, vec, valid, sbase;
 };
 
-template <int NIN, int TR, int TC, int KIND>
+// Row shift of tile column c: its rows are r0 - shift .. r0 - shift + TR - 1.
+template <int W> FX_D int col_skew(int64_t sld, int sbase, int64_t col) {
+  return sld > 0 ? int((uint64_t(sbase) + uint64_t(col) * uint64_t(sld)) % uint64_t(W)) : 0;
+}
+
+template <int NIN, int TR, int TC, int KIND, int KW>
 FX_D IssueDesc<NIN> fetch_item(const BatchMat* mats, const BatchItem* items, int64_t it,
                                bool valid) {
   IssueDesc<NIN> d;
@@ -101,13 +116,15 @@ FX_D IssueDesc<NIN> fetch_item(const BatchMat* mats, const BatchItem* items, int
   d.C = m.cols;
   // 32-bit: a batch matrix has fewer than 2^31 tiles (64-bit division is a
   // long instruction sequence, executed here by every thread for every item)
-  const uint32_t tiles_r = uint32_t((d.R + TR - 1) / TR);
+  const uint32_t tiles_r = uint32_t((d.R + KW - 1 + TR - 1) / TR);  // rows plus the largest skew
   const uint32_t tc = uint32_t(w.tile) / tiles_r;
   d.r0 = int64_t(uint32_t(w.tile) - tc * tiles_r) * TR;
   d.c0 = int64_t(tc) * TC;
   d.item = it;
   d.mat = w.mat;
   d.vec = m.vec;
+  d.sld = m.skew ? m.ld[m.skew - 1] : 0;
+  d.sbase = m.sbase;
   return d;
 }
 
@@ -120,7 +137,7 @@ FX_D IssueDesc<NIN> fetch_item(const BatchMat* mats, const BatchItem* items, int
 // TC + 1 elements. Offsets are 32-bit: a batch matrix holds fewer than
 // 2^31 elements.
 template <class LL, int TR, int TC, int NT, int NIN, int I = 0>
-FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d, bool full) {
+FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
     using T = typename L::elem;
@@ -128,65 +145,72 @@ FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d, bool full) {
     const int ld = int(d.ld[L::slot]);
     const int rr = int(d.R - d.r0), cc = int(d.C - d.c0);  // rows / cols left in the matrix
     if constexpr (L::mode == MN) {
-      const T* src = static_cast<const T*>(d.p[L::slot]) + d.r0 + d.c0 * int64_t(ld);
+      // column c holds rows r0 - s_c .. r0 - s_c + TR - 1 (s_c its skew)
+      const T* src = static_cast<const T*>(d.p[L::slot]) + d.c0 * int64_t(ld);
       constexpr int W = 16 / int(sizeof(T));
       constexpr int CPC = TR / W;  // chunks per column
       static_assert(NT % CPC == 0 && TC % (NT / CPC) == 0, "chunk copy shape");
-      const int r = (threadIdx.x % CPC) * W;
+      const int q = (threadIdx.x % CPC) * W;
+      const int R = int(d.R);
 #pragma unroll
       for (int c = threadIdx.x / CPC; c < TC; c += NT / CPC) {
-        const T* s = src + r + c * ld;
-        T* t = dst + c * TR + r;
-        if (full || (c < cc && r + W <= rr)) {
-          if ((reinterpret_cast<uintptr_t>(s) & 15) == 0) {
-            cpa::copy16(t, s);
-          } else {
+        if (c >= cc) break;
+        const int row = int(d.r0) - col_skew<W>(d.sld, d.sbase, d.c0 + c) + q;
+        const T* s = src + row + c * ld;
+        T* t = dst + c * TR + q;
+        if (row >= 0 && row + W <= R && (reinterpret_cast<uintptr_t>(s) & 15) == 0) {
+          cpa::copy16(t, s);
+        } else {
 #pragma unroll
-            for (int j = 0; j < W; ++j) cpa::copy<int(sizeof(T))>(t + j, s + j);
-          }
-        } else if (c < cc) {
-          for (int j = 0; j < W && r + j < rr; ++j) cpa::copy<int(sizeof(T))>(t + j, s + j);
+          for (int j = 0; j < W; ++j)
+            if (row + j >= 0 && row + j < R) cpa::copy<int(sizeof(T))>(t + j, s + j);
         }
       }
     } else if constexpr (L::mode == MT) {
+      // output rows r0 - (W - 1) .. r0 + TR - 1: stored row k is output row
+      // r0 - (W - 1) + k, i.e. D's column of that index
+      constexpr int W = 16 / int(sizeof(T));
       static_assert(NT % TC == 0, "transposed copy shape");
-      const T* src = static_cast<const T*>(d.p[L::slot]) + d.c0 + d.r0 * int64_t(ld);
-      const int c = threadIdx.x % TC;  // D element (c0 + c, r0 + r)
-      if (full) {
-#pragma unroll
-        for (int r = threadIdx.x / TC; r < TR; r += NT / TC)
-          cpa::copy<int(sizeof(T))>(dst + r * (TC + 1) + c, src + c + r * ld);
-      } else if (c < cc) {
-        for (int r = threadIdx.x / TC; r < TR && r < rr; r += NT / TC)
-          cpa::copy<int(sizeof(T))>(dst + r * (TC + 1) + c, src + c + r * ld);
+      const int64_t rlo = d.r0 - (W - 1);
+      const T* src = static_cast<const T*>(d.p[L::slot]) + d.c0 + rlo * int64_t(ld);
+      const int c = threadIdx.x % TC;  // D element (c0 + c, rlo + k)
+      if (c < cc) {
+        for (int k = threadIdx.x / TC; k < TR + W - 1; k += NT / TC) {
+          const int64_t row = rlo + k;
+          if (row >= 0 && row < d.R)
+            cpa::copy<int(sizeof(T))>(dst + k * (TC + 1) + c, src + c + int64_t(k) * ld);
+        }
       }
     }
-    issue_tile<LL, TR, TC, NT, NIN, I + 1>(buf, d, full);
+    issue_tile<LL, TR, TC, NT, NIN, I + 1>(buf, d);
   }
 }
 
-// Rows r..r+V-1 of tile column c of every leaf.
+// Slots i..i+V-1 of tile column c of every leaf (skew sk: output rows
+// r0 - sk + i ..; lanes outside the matrix are marked in `ok`).
 template <class LL, int V, class CT, int TR, int TC, int I = 0>
 FX_D void load_tile_vec(Pack<LL, V, CT>& p, const char* buf, const BatchMat& m, int64_t r0,
-                        int64_t c0, int r, int c, int nvalid) {
+                        int64_t c0, int i, int c, int sk, const bool (&ok)[V]) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
     using T = typename L::elem;
+    constexpr int W = 16 / int(sizeof(T));
     const T* b = reinterpret_cast<const T*>(buf + abuf_offset<LL, TR, TC, I>());
     auto& dst = pget<I>::of(p);
     if constexpr (L::mode == MN) {
-      dst = *reinterpret_cast<const Raw<T, V>*>(b + c * TR + r);
+      dst = *reinterpret_cast<const Raw<T, V>*>(b + c * TR + i);
     } else if constexpr (L::mode == MT) {
 #pragma unroll
-      for (int j = 0; j < V; ++j) dst.v[j] = to_compute<CT>(b[(r + j) * (TC + 1) + c]);
+      for (int j = 0; j < V; ++j)
+        dst.v[j] = to_compute<CT>(b[(i + j - sk + W - 1) * (TC + 1) + c]);
     } else if constexpr (L::mode == MBC) {
-      const T* q = static_cast<const T*>(m.p[L::slot]) + (r0 + r);
+      const T* q = static_cast<const T*>(m.p[L::slot]) + (r0 - sk + i);
 #pragma unroll
-      for (int j = 0; j < V; ++j) dst.v[j] = j < nvalid ? sload(q + j) : T(0.0f);
+      for (int j = 0; j < V; ++j) dst.v[j] = ok[j] ? sload(q + j) : T(0.0f);
     } else {
       dst.v[0] = sload(static_cast<const T*>(m.p[L::slot]) + (c0 + c));
     }
-    load_tile_vec<LL, V, CT, TR, TC, I + 1>(p, buf, m, r0, c0, r, c, nvalid);
+    load_tile_vec<LL, V, CT, TR, TC, I + 1>(p, buf, m, r0, c0, i, c, sk, ok);
   }
 }
 
@@ -197,20 +221,20 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
   using LL = leaves_t<E>;
   using CT = ct_of<E>;
   constexpr int AB = abuf_bytes<LL, TR, TC>();
+  constexpr int V = 16 / int(sizeof(T));  // also the largest row skew + 1
   extern __shared__ __align__(128) char smem[];
   TileDesc* desc = reinterpret_cast<TileDesc*>(smem + NBUF * AB);
   const int64_t G = gridDim.x;
   const int64_t mine = nitems > int64_t(blockIdx.x) ? (nitems - blockIdx.x + G - 1) / G : 0;
   auto fetch = [&](int64_t j) {
-    return fetch_item<NIN, TR, TC, KIND>(mats, items, blockIdx.x + j * G, j < mine);
+    return fetch_item<NIN, TR, TC, KIND, V>(mats, items, blockIdx.x + j * G, j < mine);
   };
   // issue a fetched item into buffer b (every thread commits a group, even an empty one)
   auto issue = [&](const IssueDesc<NIN>& d, int b) {
     if (d.valid) {
-      const bool full = d.r0 + TR <= d.R && d.c0 + TC <= d.C;
-      issue_tile<LL, TR, TC, NT, NIN>(smem + b * AB, d, full);
+      issue_tile<LL, TR, TC, NT, NIN>(smem + b * AB, d);
       if (threadIdx.x == 0)
-        desc[b] = TileDesc{d.z, d.ldz, d.R, d.C, d.r0, d.c0, d.item, d.mat, 1};
+        desc[b] = TileDesc{d.z, d.ldz, d.R, d.C, d.r0, d.c0, d.item, d.sld, d.mat, 1, d.sbase};
     }
     cpa::commit();
   };
@@ -225,31 +249,39 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
     const int b = int(j % NBUF);
     const TileDesc d = desc[b];
     const BatchMat& m = mats[d.mat];
-    // V consecutive rows of one column per step; a thread adds at most
-    // TR*TC/NT values of a tile: a plain sum, merged compensated per warp
-    constexpr int V = 16 / int(sizeof(T));
+    // V consecutive slots of one column per step (column c's rows start at
+    // r0 - skew); a thread adds at most TR*TC/NT values of a tile: a plain
+    // sum, merged compensated per warp
     constexpr int RG = TR / V;  // row groups per column
     static_assert(NT % RG == 0 && TC % (NT / RG) == 0, "consumer shape");
     CT tsum = CT(0);
     const char* buf = smem + b * AB;
-    const int r = (threadIdx.x % RG) * V;
-    const int rr = int(d.R - d.r0), cc = int(d.C - d.c0);
-    const int nvalid = clamp_valid(rr - r, V);
-    T* z = KIND != FX_KIND_FULL_REDUCE
-               ? static_cast<T*>(const_cast<void*>(d.z)) + d.r0 + d.c0 * d.ldz
-               : nullptr;
+    const int i = (threadIdx.x % RG) * V;
+    const int cc = int(d.C - d.c0);
+    const int R = int(d.R);
+    T* z = KIND != FX_KIND_FULL_REDUCE ? static_cast<T*>(const_cast<void*>(d.z)) : nullptr;
     const int ldz = int(d.ldz);
-    if (nvalid > 0) {
 #pragma unroll
-      for (int c = threadIdx.x / RG; c < TC; c += NT / RG) {
-        if (c < cc) {
+    for (int c = threadIdx.x / RG; c < TC; c += NT / RG) {
+      if (c < cc) {
+        const int sk = col_skew<V>(d.sld, d.sbase, d.c0 + c);
+        const int row = int(d.r0) - sk + i;  // output row of slot i
+        bool ok[V];
+        bool all = true, any = false;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          ok[j] = row + j >= 0 && row + j < R;
+          all = all && ok[j];
+          any = any || ok[j];
+        }
+        if (any) {
           Pack<LL, V, CT> p;
-          load_tile_vec<LL, V, CT, TR, TC>(p, buf, m, d.r0, d.c0, r, c, nvalid);
+          load_tile_vec<LL, V, CT, TR, TC>(p, buf, m, d.r0, d.c0, i, c, sk, ok);
           CT v[V];
           eval_lanes<V>(e, p, v);
           if constexpr (KIND != FX_KIND_FULL_REDUCE) {
-            T* q = z + r + c * ldz;
-            if (nvalid == V && (reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+            T* q = z + row + (d.c0 + c) * int64_t(ldz);
+            if (all && (reinterpret_cast<uintptr_t>(q) & 15) == 0) {
               Raw<T, V> o;
 #pragma unroll
               for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(v[j]);
@@ -257,13 +289,13 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
             } else {
 #pragma unroll
               for (int j = 0; j < V; ++j)
-                if (j < nvalid) sstore(q + j, narrow_to<T>::from(v[j]));
+                if (ok[j]) sstore(q + j, narrow_to<T>::from(v[j]));
             }
           }
           if constexpr (KIND != FX_KIND_ELEMENTWISE) {
 #pragma unroll
             for (int j = 0; j < V; ++j)
-              if (j < nvalid) tsum += v[j];
+              if (ok[j]) tsum += v[j];
           }
         }
       }
@@ -364,6 +396,26 @@ bool batch_leaf_check(const fx_batch_item& it, int64_t R, int64_t C, bool& vec, 
   return true;
 }
 
+// Plain leaves of a batch matrix: one leading dimension, one base alignment
+// modulo `align` bytes? `first` receives the first plain leaf's slot.
+template <class LL, int I = 0> bool skew_check(const BatchMat& m, int& first, int align) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    if constexpr (L::mode == MN) {
+      const int k = L::slot;
+      if (first < 0) {
+        first = k;
+      } else if (m.ld[k] != m.ld[first] ||
+                 reinterpret_cast<uintptr_t>(m.p[k]) % uintptr_t(align) !=
+                     reinterpret_cast<uintptr_t>(m.p[first]) % uintptr_t(align)) {
+        return false;
+      }
+    }
+    return skew_check<LL, I + 1>(m, first, align);
+  }
+  return true;
+}
+
 // A leaf's ld of 0 in an item means its own row count.
 template <class LL, int I = 0> void fill_default_ld(BatchMat& m, int64_t R, int64_t C) {
   if constexpr (I < tl_size<LL>::value) {
@@ -449,7 +501,23 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
         m.rows = R;
         m.cols = C;
         m.vec = vec ? 1 : 0;
-        const int64_t nt = ((R + TR - 1) / TR) * ((C + TCc - 1) / TCc);
+        // skewed tiles when every plain leaf and Z share ld and base alignment
+        {
+          constexpr int W = 16 / int(sizeof(T));
+          int first = -1;
+          bool ok = skew_check<LL>(m, first, W * int(sizeof(T)));
+          if (ok && first >= 0 && has_z) {
+            const uintptr_t a0 = reinterpret_cast<uintptr_t>(m.p[first]) % uintptr_t(W * sizeof(T));
+            ok = m.ld[zs] == m.ld[first] &&
+                 reinterpret_cast<uintptr_t>(m.p[zs]) % uintptr_t(W * sizeof(T)) == a0;
+          }
+          m.skew = (ok && first >= 0) ? first + 1 : 0;
+          m.sbase = m.skew ? int((reinterpret_cast<uintptr_t>(m.p[first]) / sizeof(T)) % W) : 0;
+        }
+        // row tiles cover R plus the largest skew (W - 1 rows)
+        const int64_t nt = (R > 0 && C > 0)
+                               ? ((R + 16 / int64_t(sizeof(T)) - 1 + TR - 1) / TR) * ((C + TCc - 1) / TCc)
+                               : 0;
         m.first = int64_t(work.size());
         m.ntiles = int32_t(nt);
         for (int64_t t = 0; t < nt; ++t) work.push_back(BatchItem{int32_t(i), int32_t(t)});

@@ -114,8 +114,14 @@ struct OpSquare {
   template <class C> static FX_D C f(C a) { return a * a; }
   template <class C> static FX_D C d(C a, C) { return C(2) * a; }
 };
+// exp inside sigmoid: CUDA's fast __expf for FP32 (its error, a few ulp
+// plus |x| * 2^-23 relative from scaling x by log2(e), is further damped by
+// the factor 1 - sigmoid in the result), exp for FP64.
+FX_D float m_exp_sig(float x) { return __expf(x); }
+FX_D double m_exp_sig(double x) { return ::exp(x); }
+
 struct OpSigmoid {  // Sec. 4: sigmoid = 1 / (1 + exp(-X))
-  template <class C> static FX_D C f(C a) { return m_rcp(C(1) + m_exp(-a)); }
+  template <class C> static FX_D C f(C a) { return m_rcp(C(1) + m_exp_sig(-a)); }
   template <class C> static FX_D C d(C, C z) { return z * (C(1) - z); }
 };
 struct OpTanh {
