@@ -51,10 +51,10 @@ METRIC = "fused-expr effective HBM GB/s (% of GB300 peak) and speedup vs unfused
 # DRAM traffic per launch of a dominant kernel from an ncu capture (bytes),
 # valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first
-    # timed launch of Z at 8192^2 FP32 (profiles/k_flat_schur_sqrt_sigmoid_f32.md):
-    # 1,073,779,456 read + 215,429,632 written (the rest of Z still in L2)
-    ("expr8192", "Z"): {"bytes": 1073779456 + 215429632, "hash": "72571fe488c04e3e"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on a warm
+    # launch of Z at 8192^2 FP32 (profiles/k_flat_schur_sqrt_sigmoid_f32.md):
+    # 1,073,778,688 read + 215,230,720 written (the rest of Z still in L2)
+    ("expr8192", "Z"): {"bytes": 1073778688 + 215230720, "hash": "739eb18fa6a7e2bd"},
 }
 
 # FP64-pipe instructions per output element of FP64 trees (per lane: DFMA,

@@ -214,6 +214,24 @@ FX_D void load_tile_vec(Pack<LL, V, CT>& p, const char* buf, const BatchMat& m, 
   }
 }
 
+// Per-warp tile partials: FP32 pairs for FP32 trees (no FP64 conversion on
+// the hot kernel's slow FP64 pipe; the combine widens them), FP64 pairs for
+// FP64 trees. The partial buffer holds double2 slots either way.
+FX_D void store_partial(double2* part, int64_t i, float s, float c) {
+  reinterpret_cast<float2*>(part)[i] = make_float2(s, c);
+}
+FX_D void store_partial(double2* part, int64_t i, double s, double c) {
+  part[i] = make_double2(s, c);
+}
+template <class RT> FX_D double2 load_partial(const double2* part, int64_t i) {
+  if constexpr (std::is_same<RT, double>::value) {
+    return __ldcg(part + i);
+  } else {
+    const float2 f = __ldcg(reinterpret_cast<const float2*>(part) + i);
+    return make_double2(double(f.x), double(f.y));
+  }
+}
+
 template <class E, class T, int TR, int TC, int NT, int NBUF, int KIND, int NIN>
 __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* __restrict__ mats,
                                                     const BatchItem* __restrict__ items,
@@ -307,7 +325,7 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
       st.c = CT(0);
       warp_merge(st);
       if ((threadIdx.x & 31) == 0)
-        part[d.item * (NT / 32) + threadIdx.x / 32] = make_double2(double(st.s), double(st.c));
+        store_partial(part, d.item * (NT / 32) + threadIdx.x / 32, st.s, st.c);
     }
     __syncthreads();  // buffer b is free for the item issued next
   }
@@ -327,7 +345,7 @@ __global__ void __launch_bounds__(256) k_batch_combine(const BatchMat* __restric
   std::conditional_t<std::is_same<RT, double>::value, CompSum<double>, PlainSum<double>> a;
   a.init();
   for (int64_t k = lane; k < int64_t(m.ntiles) * nw; k += 32) {
-    double2 q = __ldcg(part + m.first * nw + k);
+    const double2 q = load_partial<RT>(part, m.first * nw + k);
     a.add(q.x);
     a.add(q.y);
   }
