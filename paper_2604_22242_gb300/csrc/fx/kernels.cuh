@@ -187,6 +187,7 @@ template <class T, int V> struct EpiStore {
   int64_t ldz;
   static constexpr bool stores = true;
   static constexpr bool reduces = false;
+  static constexpr bool pure_sum = false;
   static constexpr bool sqrt_result = false;
   struct State {
     FX_D void init() {}
@@ -210,6 +211,14 @@ template <class CTy, int V, bool SQ> struct EpiSum {
   int64_t ldz;
   static constexpr bool stores = false;
   static constexpr bool reduces = true;
+  static constexpr bool pure_sum = true;  // k_flat may combine several vectors per add
+  // the (squared) lanes of one full vector, summed pairwise
+  template <class CT> FX_D CT vsum(const CT (&v)[V]) const {
+    CT w[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) w[j] = SQ ? v[j] * v[j] : v[j];
+    return lane_sum(w);
+  }
   static constexpr bool sqrt_result = SQ;
   using State = ThreadSum<CTy>;
   template <class CT> FX_D void put(State& st, int64_t, const CT (&v)[V], int nvalid) const {
@@ -232,6 +241,7 @@ template <class T, int V> struct EpiStoreSum {
   int64_t ldz;
   static constexpr bool stores = true;
   static constexpr bool reduces = true;
+  static constexpr bool pure_sum = false;
   static constexpr bool sqrt_result = false;
   using State = ThreadSum<compute_t<T>>;
   template <class CT> FX_D void put(State& st, int64_t off, const CT (&v)[V], int nvalid) const {
@@ -369,13 +379,29 @@ __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const i
         load_flat(p[u], sl, vi * V, r, c);
       }
     }
+    if constexpr (Epi::pure_sum) {
+      // one compensated add per step: the U vectors' sums added pairwise
+      CT vs[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t vi = b + u * bdim;
-      if (vi < nv) {
-        CT v[V];
-        eval_lanes<V>(e, p[u], v);
-        epi.put(st, vi * V, v, V);
+      for (int u = 0; u < U; ++u) {
+        const int64_t vi = b + u * bdim;
+        vs[u] = CT(0);
+        if (vi < nv) {
+          CT v[V];
+          eval_lanes<V>(e, p[u], v);
+          vs[u] = epi.vsum(v);
+        }
+      }
+      st.add(lane_sum(vs));
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t vi = b + u * bdim;
+        if (vi < nv) {
+          CT v[V];
+          eval_lanes<V>(e, p[u], v);
+          epi.put(st, vi * V, v, V);
+        }
       }
     }
   }
@@ -594,26 +620,32 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
           const int nv = clamp_valid(R - r, V);
           if (nv > 0) load_rc(p[u], sl, r, c, nv);
         }
+        // sums: the U vectors' lanes are added pairwise into one value per
+        // step, then one compensated add (short dependency chains, which
+        // matter for FP64 adds)
+        CT vs[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int64_t r = rb + int64_t(u) * G * V;
           const int nv = clamp_valid(R - r, V);
+          vs[u] = CT(0);
           if (nv > 0) {
             CT v[V];
             eval_lanes<V>(e, p[u], v);
-            if (!ISMAX && nv == V) {
-              acc.add(lane_sum(v));
+            if (ISMAX) {
+#pragma unroll
+              for (int j = 0; j < V; ++j)
+                if (j < nv) m = max_nan(m, v[j]);
+            } else if (nv == V) {
+              vs[u] = lane_sum(v);
             } else {
 #pragma unroll
-              for (int j = 0; j < V; ++j) {
-                if (j < nv) {
-                  if (ISMAX) m = max_nan(m, v[j]);
-                  else acc.add(v[j]);
-                }
-              }
+              for (int j = 0; j < V; ++j)
+                if (j < nv) vs[u] += v[j];
             }
           }
         }
+        if (!ISMAX) acc.add(lane_sum(vs));
       }
     }
     CT res;
