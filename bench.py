@@ -53,8 +53,8 @@ METRIC = "fused-expr effective HBM GB/s (% of GB300 peak) and speedup vs unfused
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on a warm
     # launch of Z at 8192^2 FP32 (profiles/k_flat_schur_sqrt_sigmoid_f32.md):
-    # 1,073,778,688 read + 215,230,720 written (the rest of Z still in L2)
-    ("expr8192", "Z"): {"bytes": 1073778688 + 215230720, "hash": "739eb18fa6a7e2bd"},
+    # 1,073,779,200 read + 215,079,936 written (the rest of Z still in L2)
+    ("expr8192", "Z"): {"bytes": 1073779200 + 215079936, "hash": "0941fe1e72e492c0"},
 }
 
 # FP64-pipe instructions per output element of FP64 trees (per lane: DFMA,
