@@ -189,7 +189,8 @@ fx_status fx_eval_backward(fx_expr* x, const void* grad_out, void* const* grad_p
  * cached choice for this (expression, storage, shape class, device) if the
  * cache file has one. FX_TUNE_SEARCH: time every candidate launch shape
  * on the currently bound buffers (writes the outputs; synchronises the
- * stream), keep the fastest, and record it in the cache file
+ * stream), keep the fastest (the built-in shape unless a candidate is at
+ * least 1% faster than it), and record it in the cache file
  * ($FX_TUNE_CACHE, default ./fx_tune.json). */
 fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream);
 

@@ -153,6 +153,7 @@ fx_status run_unfused(fx_expr* x, const Root& root, int kind, cudaStream_t st,
   using E = typename root_of<Root>::inner;
   using LL = leaves_t<E>;
   Run r = over ? *over : run_of(x, st);
+  r.tune = Tune{};  // one-operator kernels at the library's default shapes, whatever the tree's tuning
   const E& e = inner_of(root);
   int64_t R = 0, C = 0;
   if (!infer_shape<LL>(r.b, R, C)) return fail(FX_E_SHAPE, "no matrix leaf to take the shape from");
