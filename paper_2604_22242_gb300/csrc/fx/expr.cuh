@@ -35,7 +35,7 @@ FX_HD constexpr int flip_mode(int m) {
 // ---------------------------------------------------------------- operators
 //
 // Each operator tag has the element function f and the partial derivatives
-// used by the fused backward pass (bwd.cuh).
+// used by the fused backward pass (k_bwd, k_bwd_bulk).
 
 FX_D float m_exp(float x) { return ::expf(x); }
 FX_D double m_exp(double x) { return ::exp(x); }
@@ -133,6 +133,15 @@ struct OpTanh {
 
 struct ExprBase {};
 
+// Reverse mode over one element: fwd(c) evaluates every node of the tree
+// once and keeps each node's value with its children's (a tape held in
+// registers); rev(tape, adj, g) walks the same values back down, giving
+// each leaf its adjoint. bwd(c, adj, g) is the two passes in a row.
+template <class CT, class... Ch> struct Tape;
+template <class CT> struct Tape<CT> { CT v; };
+template <class CT, class A> struct Tape<CT, A> { CT v; A a; };
+template <class CT, class A, class B> struct Tape<CT, A, B> { CT v; A a; B b; };
+
 template <int K, class T, int M = MN> struct Leaf : ExprBase {
   static_assert(K >= 0 && K < FX_MAX_SLOTS, "slot out of range");
   using elem = T;
@@ -140,6 +149,10 @@ template <int K, class T, int M = MN> struct Leaf : ExprBase {
   static constexpr int mode = M;
   template <class Ctx> FX_D typename Ctx::CT ev(const Ctx& c) const {
     return c.template leaf<K, M>();
+  }
+  template <class Ctx> FX_D Tape<typename Ctx::CT> fwd(const Ctx& c) const { return {ev(c)}; }
+  template <class CT, class Tp, class G> FX_D void rev(const Tp&, CT adj, G& g) const {
+    g.template add<K, M>(adj);
   }
   template <class Ctx, class G>
   FX_D void bwd(const Ctx&, typename Ctx::CT adj, G& g) const {
@@ -153,25 +166,37 @@ template <class Op, class L, class R> struct Bin : ExprBase {
   template <class Ctx> FX_D typename Ctx::CT ev(const Ctx& c) const {
     return Op::f(l.ev(c), r.ev(c));
   }
+  template <class Ctx> FX_D auto fwd(const Ctx& c) const {
+    const auto a = l.fwd(c);
+    const auto b = r.fwd(c);
+    return Tape<typename Ctx::CT, decltype(a), decltype(b)>{Op::f(a.v, b.v), a, b};
+  }
+  template <class CT, class Tp, class G> FX_D void rev(const Tp& t, CT adj, G& g) const {
+    CT da, db;
+    Op::d(t.a.v, t.b.v, da, db);
+    l.rev(t.a, CT(adj * da), g);
+    r.rev(t.b, CT(adj * db), g);
+  }
   template <class Ctx, class G>
   FX_D void bwd(const Ctx& c, typename Ctx::CT adj, G& g) const {
-    using CT = typename Ctx::CT;
-    CT a = l.ev(c), b = r.ev(c), da, db;
-    Op::d(a, b, da, db);
-    l.bwd(c, adj * da, g);
-    r.bwd(c, adj * db, g);
+    rev(fwd(c), adj, g);
   }
 };
 
 template <class Op, class E> struct Un : ExprBase {
   E e;
   template <class Ctx> FX_D typename Ctx::CT ev(const Ctx& c) const { return Op::f(e.ev(c)); }
+  template <class Ctx> FX_D auto fwd(const Ctx& c) const {
+    const auto a = e.fwd(c);
+    return Tape<typename Ctx::CT, decltype(a)>{Op::f(a.v), a};
+  }
+  // the derivative may use the node's own value z = f(a) (exp, sigmoid, tanh)
+  template <class CT, class Tp, class G> FX_D void rev(const Tp& t, CT adj, G& g) const {
+    e.rev(t.a, CT(adj * Op::d(t.a.v, t.v)), g);
+  }
   template <class Ctx, class G>
   FX_D void bwd(const Ctx& c, typename Ctx::CT adj, G& g) const {
-    using CT = typename Ctx::CT;
-    CT a = e.ev(c);
-    CT z = Op::f(a);
-    e.bwd(c, adj * Op::d(a, z), g);
+    rev(fwd(c), adj, g);
   }
 };
 
@@ -183,12 +208,19 @@ template <class Op, class E> struct SL : ExprBase {
     using CT = typename Ctx::CT;
     return Op::f(CT(s), e.ev(c));
   }
+  template <class Ctx> FX_D auto fwd(const Ctx& c) const {
+    using CT = typename Ctx::CT;
+    const auto b = e.fwd(c);
+    return Tape<CT, decltype(b)>{Op::f(CT(s), b.v), b};
+  }
+  template <class CT, class Tp, class G> FX_D void rev(const Tp& t, CT adj, G& g) const {
+    CT da, db;
+    Op::d(CT(s), t.a.v, da, db);
+    e.rev(t.a, CT(adj * db), g);
+  }
   template <class Ctx, class G>
   FX_D void bwd(const Ctx& c, typename Ctx::CT adj, G& g) const {
-    using CT = typename Ctx::CT;
-    CT b = e.ev(c), da, db;
-    Op::d(CT(s), b, da, db);
-    e.bwd(c, adj * db, g);
+    rev(fwd(c), adj, g);
   }
 };
 template <class Op, class E> struct SR : ExprBase {
@@ -198,12 +230,19 @@ template <class Op, class E> struct SR : ExprBase {
     using CT = typename Ctx::CT;
     return Op::f(e.ev(c), CT(s));
   }
+  template <class Ctx> FX_D auto fwd(const Ctx& c) const {
+    using CT = typename Ctx::CT;
+    const auto a = e.fwd(c);
+    return Tape<CT, decltype(a)>{Op::f(a.v, CT(s)), a};
+  }
+  template <class CT, class Tp, class G> FX_D void rev(const Tp& t, CT adj, G& g) const {
+    CT da, db;
+    Op::d(t.a.v, CT(s), da, db);
+    e.rev(t.a, CT(adj * da), g);
+  }
   template <class Ctx, class G>
   FX_D void bwd(const Ctx& c, typename Ctx::CT adj, G& g) const {
-    using CT = typename Ctx::CT;
-    CT a = e.ev(c), da, db;
-    Op::d(a, CT(s), da, db);
-    e.bwd(c, adj * da, g);
+    rev(fwd(c), adj, g);
   }
 };
 
