@@ -52,11 +52,15 @@ METRIC = "fused-expr effective HBM GB/s (% of GB300 peak) and speedup vs unfused
 # valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first
-    # timed launch of Z at 8192^2 FP32, 256 threads, 4 vectors per leaf
-    # (profiles/k_flat_schur_sqrt_sigmoid_f32.md): 1,073,795,840 read +
-    # 215,948,800 written (the rest of Z still in L2 when the launch ends)
-    ("expr8192", "Z"): {"bytes": 1073795840 + 215948800, "hash": "269130ee5a918783",
-                        "shape": (256, 4, 0, 0)},
+    # timed launch of Z at 8192^2 FP32 (profiles/k_flat_schur_sqrt_sigmoid_f32.md),
+    # per (threads per block, vectors per leaf) of the register kernel k_flat
+    # (pipelines 0 and 2 of this four-leaf tree; the blocks-per-SM cap only
+    # changes the grid of the same streaming loop). Unroll 2: 1,073,772,800
+    # read + 241,834,496 written; unroll 4: 1,073,857,024 + 241,025,024 (the
+    # rest of Z still in L2 when the launch ends).
+    ("expr8192", "Z"): {"hash": "ea360771f9e42b1e",
+                        "bytes": {(256, 2): 1073772800 + 241834496,
+                                  (256, 4): 1073857024 + 241025024}},
 }
 
 # FP64-pipe instructions per output element of FP64 trees (per lane: DFMA,
@@ -554,10 +558,11 @@ def run_ours(args, rank, world):
     dom_op = next(o for o in ops if o.key == dom)
     z_gbs = dom_op.bytes / (per_ms[dom] / 1e3) / 1e9
     tr = TRAFFIC.get((args.workload, dom))
-    traffic = tr["bytes"] if tr and tr["hash"] == kernel_source_hash() else None
-    if traffic is not None and dom in handles and \
-            tuple(fx.fx_expr_launch_shape(handles[dom])) != tr["shape"]:
-        traffic = None   # counted at another launch shape
+    traffic = None
+    if tr and tr["hash"] == kernel_source_hash() and dom in handles:
+        block, unroll, _, pipe = fx.fx_expr_launch_shape(handles[dom])
+        if pipe != 1:   # null when counted at another launch shape or kernel
+            traffic = tr["bytes"].get((block, unroll))
     cpu = cpu_all = None
     if world == 1 and args.workload == "expr8192" and args.size == 8192 and not args.no_cpu:
         t_cpu, b_cpu = cpu_oracle_time(8192, args.cpu_cols, "f32")

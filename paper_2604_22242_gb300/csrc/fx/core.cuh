@@ -70,6 +70,10 @@ template <class T, int V> struct alignas(sizeof(T) * V) Raw {
 };
 
 // Read-only streaming loads: non-coherent path, no L1 allocation.
+// Vector stores stream (.cs, evict-first): an output element is written
+// once, and dirty lines left in L2 are written back during the next
+// kernel, slowing its reads (measured on GB300: a reduction that follows a
+// 1 GB element-wise tree took 6% longer with plain stores).
 template <int B> struct Mem;
 template <> struct Mem<32> {
   template <class R> static FX_D void ld(R& r, const void* p) {
@@ -81,7 +85,7 @@ template <> struct Mem<32> {
   }
   template <class R> static FX_D void st(void* p, const R& r) {
     const uint32_t* w = reinterpret_cast<const uint32_t*>(&r);
-    asm volatile("st.global.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]),
+    asm volatile("st.global.cs.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]),
                  "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
                  : "memory");
   }
@@ -95,7 +99,7 @@ template <> struct Mem<16> {
   }
   template <class R> static FX_D void st(void* p, const R& r) {
     const uint32_t* w = reinterpret_cast<const uint32_t*>(&r);
-    asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(w[0]), "r"(w[1]),
                  "r"(w[2]), "r"(w[3])
                  : "memory");
   }
@@ -107,7 +111,7 @@ template <> struct Mem<8> {
   }
   template <class R> static FX_D void st(void* p, const R& r) {
     const uint32_t* w = reinterpret_cast<const uint32_t*>(&r);
-    asm volatile("st.global.v2.u32 [%0], {%1,%2};" ::"l"(p), "r"(w[0]), "r"(w[1]) : "memory");
+    asm volatile("st.global.cs.v2.u32 [%0], {%1,%2};" ::"l"(p), "r"(w[0]), "r"(w[1]) : "memory");
   }
 };
 template <> struct Mem<4> {
