@@ -145,7 +145,10 @@ fx_status fx_eval(fx_expr* x, void* stream);
 
 /* The same tree evaluated one operator at a time (one kernel per node,
  * every intermediate materialised in the storage type in library
- * workspace): the unfused baseline the fused path is measured against. */
+ * workspace): the unfused baseline the fused path is measured against.
+ * Its kernels always run at the library's default launch shapes; a shape
+ * set by fx_tune or fx_expr_set_launch_shape applies to the fused path
+ * only. */
 fx_status fx_eval_unfused(fx_expr* x, void* stream);
 
 /* End-to-end evaluation from and to HOST memory. The slots must be bound
