@@ -71,6 +71,20 @@ TRAFFIC = {
 FP64_PIPE_OPS = {("expr8192_f64", "Z"): 35}
 
 
+def recorded_traffic(workload, dom, shape, source_hash):
+    """DRAM bytes per launch recorded for the dominant tree, or None when the
+    kernel sources changed since the capture, the launch shape (block,
+    unroll, blocks/SM, pipeline) was not captured, or pipeline 1 selected the
+    bulk-copy kernel instead of the register kernel."""
+    tr = TRAFFIC.get((workload, dom))
+    if not tr or tr["hash"] != source_hash:
+        return None
+    block, unroll, _, pipe = shape
+    if pipe == 1:
+        return None
+    return tr["bytes"].get((block, unroll))
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("core.cuh", "expr.cuh", "plan.cuh", "kernels.cuh"):
@@ -557,12 +571,10 @@ def run_ours(args, rank, world):
     peak, peak_kind = measured_peak()
     dom_op = next(o for o in ops if o.key == dom)
     z_gbs = dom_op.bytes / (per_ms[dom] / 1e3) / 1e9
-    tr = TRAFFIC.get((args.workload, dom))
     traffic = None
-    if tr and tr["hash"] == kernel_source_hash() and dom in handles:
-        block, unroll, _, pipe = fx.fx_expr_launch_shape(handles[dom])
-        if pipe != 1:   # null when counted at another launch shape or kernel
-            traffic = tr["bytes"].get((block, unroll))
+    if dom in handles:
+        traffic = recorded_traffic(args.workload, dom, fx.fx_expr_launch_shape(handles[dom]),
+                                   kernel_source_hash())
     cpu = cpu_all = None
     if world == 1 and args.workload == "expr8192" and args.size == 8192 and not args.no_cpu:
         t_cpu, b_cpu = cpu_oracle_time(8192, args.cpu_cols, "f32")

@@ -1,5 +1,6 @@
-"""The replica path of bench.py with two ranks on CPU (gloo): the slowest
-rank's time sets the whole-job number, and only rank 0 reports."""
+"""Host logic of bench.py on CPU: the replica path with two ranks (gloo),
+where the slowest rank's time sets the whole-job number and only rank 0
+reports, and the lookup of the recorded DRAM traffic."""
 import json
 import os
 import socket
@@ -61,3 +62,24 @@ def test_reference_arm_reports_on_rank0_only():
     line = json.loads(p.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_recorded_traffic_matches_source_and_shape():
+    """The dominant kernel's DRAM traffic is reported only for the kernel
+    sources and launch shapes it was captured at."""
+    import bench
+    h = bench.kernel_source_hash()
+    tr = bench.TRAFFIC[("expr8192", "Z")]
+    (block, unroll), nbytes = next(iter(tr["bytes"].items()))
+    if tr["hash"] == h:
+        assert bench.recorded_traffic("expr8192", "Z", (block, unroll, 0, 0), h) == nbytes
+        assert bench.recorded_traffic("expr8192", "Z", (block, unroll, 4, 2), h) == nbytes
+    assert bench.recorded_traffic("expr8192", "Z", (block, unroll, 0, 0), "0" * 16) is None
+    assert bench.recorded_traffic("expr8192", "Z", (block, unroll, 0, 1), tr["hash"]) is None
+    assert bench.recorded_traffic("expr8192", "Z", (96, 16, 0, 0), tr["hash"]) is None
+    assert bench.recorded_traffic("suite10k", "add16", (256, 4, 0, 0), tr["hash"]) is None
+    # every recorded figure is the same streaming pass: algorithmic reads plus
+    # at most the algorithmic writes
+    alg_read, alg_write = 4 * 8192 * 8192 * 4, 8192 * 8192 * 4
+    for b in tr["bytes"].values():
+        assert alg_read <= b <= alg_read * 1.001 + alg_write
