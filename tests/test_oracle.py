@@ -586,3 +586,73 @@ def test_gradient_sigma_bounds_float32_reverse_pass():
         got = g32[name].T.ravel().astype(np.float64) if name != "b" else g32[name].ravel()
         assert np.all(np.abs(got - v) <= 8 * u * s + 1e-300), name
         assert np.median(s / np.maximum(np.abs(v), 1e-300)) < 100, name
+
+
+# ------------------------------------------------------------ Sec. 4 trees of the suite
+
+def _suite_tree(name, scalars=None):
+    from harness import tree_of
+    return tree_of(name, scalars)
+
+
+def test_expr2_hand_values():
+    """expr2 = a*A + (B + C)^T + log(pow(D, 2)) with the suite's a = 0.75 and
+    exponent 2, on a 2x2 case worked by hand: 0.75*[[4,8],[12,16]] = [[3,6],[9,12]],
+    ([[1,2],[3,4]] + [[10,20],[30,40]])^T = [[11,33],[22,44]], log(D^2) = 0 for
+    D = +-1, so Z = [[14,39],[31,56]]; with D = e every element gains log(e^2) = 2."""
+    tree = _suite_tree("expr2")
+    A = buf([4, 12, 8, 16], 2, 2)
+    B = buf([1, 3, 2, 4], 2, 2)
+    C = buf([10, 30, 20, 40], 2, 2)
+    got = oracle.evaluate(tree, {"A": A, "B": B, "C": C, "D": buf([1, -1, -1, 1], 2, 2)})
+    assert got.T.ravel().tolist() == [14.0, 31.0, 39.0, 56.0]
+    got = oracle.evaluate(tree, {"A": A, "B": B, "C": C, "D": buf([math.e] * 4, 2, 2)})
+    assert np.allclose(got.T.ravel(), [16.0, 33.0, 41.0, 58.0], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("beta", [None, 2.5])
+def test_swish_odd_part_is_x(beta):
+    """swish(x) = x * sigmoid(beta x) (Sec. 4). Since sigmoid(t) + sigmoid(-t) = 1,
+    swish(x) - swish(-x) = x for every beta, and swish(0) = 0."""
+    tree = _suite_tree("swish", None if beta is None else [beta])
+    x = np.linspace(-6.0, 6.0, 25)
+    zp = oracle.evaluate(tree, {"X": buf(x, 25, 1)})[:, 0]
+    zm = oracle.evaluate(tree, {"X": buf(-x, 25, 1)})[:, 0]
+    assert np.allclose(zp - zm, x, rtol=0, atol=1e-14)
+    assert zp[12] == 0.0
+    assert np.all(zp[x > 0] > 0) and np.all(zp[x > 0] < x[x > 0])
+
+
+def test_gelu_odd_part_limits_and_exact_gelu():
+    """gelu = (x/2)(1 + tanh(s0 (x + s1 x^3))) (Sec. 4, s0 = sqrt(2/pi),
+    s1 = 0.044715): tanh is odd, so gelu(x) - gelu(-x) = x; gelu(0) = 0; far
+    out gelu(x) = x and gelu(-x) = 0. The tanh form approximates the exact
+    GELU x * Phi(x) = (x/2)(1 + erf(x / sqrt 2)) to within 1e-3 (without the
+    cubic term it is off by 0.03 at x = 2)."""
+    tree = _suite_tree("gelu")
+    x = np.linspace(-5.0, 5.0, 41)
+    zp = oracle.evaluate(tree, {"X": buf(x, 41, 1)})[:, 0]
+    zm = oracle.evaluate(tree, {"X": buf(-x, 41, 1)})[:, 0]
+    assert np.allclose(zp - zm, x, rtol=0, atol=1e-14)
+    assert zp[20] == 0.0
+    far = oracle.evaluate(tree, {"X": buf([30.0, -30.0], 2, 1)})[:, 0]
+    assert far[0] == 30.0 and far[1] == 0.0
+    exact = np.array([0.5 * v * (1.0 + math.erf(v / math.sqrt(2.0))) for v in x])
+    assert np.max(np.abs(zp - exact)) < 1e-3
+    no_cubic = oracle.evaluate(_suite_tree("gelu", [math.sqrt(2.0 / math.pi), 0.0]),
+                               {"X": buf([2.0], 1, 1)})[0, 0]
+    assert abs(no_cubic - 0.5 * 2.0 * (1.0 + math.erf(2.0 / math.sqrt(2.0)))) > 0.02
+
+
+def test_expr3_reduces_to_reciprocal_product():
+    """expr3 = 1 / (X % conv_to<fmat>(Y) + log(log(X + 2) % W)) (Sec. 4): with
+    W = 1 / log(X + 2) the outer log vanishes and Z = 1 / (X * fl32(Y)); Y = 0.1
+    is read as its nearest FP32 value 0.100000001490116119384765625."""
+    tree = _suite_tree("expr3")
+    X = np.array([10.0, 0.5, 3.0, 7.25])
+    Y = np.array([0.1, 4.0, -0.75, 1.0 / 3.0])
+    W = 1.0 / np.log(X + 2.0)
+    got = oracle.evaluate(tree, {"X": buf(X, 4, 1), "Y": buf(Y, 4, 1), "W": buf(W, 4, 1)})[:, 0]
+    want = 1.0 / (X * Y.astype(np.float32).astype(np.float64))
+    assert np.allclose(got, want, rtol=1e-14, atol=0)
+    assert got[0] != 1.0 / (X[0] * Y[0])       # the FP32 conversion of Y is visible
