@@ -656,3 +656,72 @@ def test_expr3_reduces_to_reciprocal_product():
     want = 1.0 / (X * Y.astype(np.float32).astype(np.float64))
     assert np.allclose(got, want, rtol=1e-14, atol=0)
     assert got[0] != 1.0 / (X[0] * Y[0])       # the FP32 conversion of Y is visible
+
+
+L3 = math.log(3.0)   # sigmoid(ln 3) = 1 / (1 + 1/3) = 3/4
+
+# Each oracle tree the parity tests compare against (as tests/harness.py
+# writes it, default scalars), on a small case worked by hand from the
+# paper's definitions. Leaves: (column-major values, rows, cols).
+HAND_TREES = {
+    # A%B + 3.5*exp(C) - D^T: [[2,4],[6,8]] + 3.5 - [[0,2],[1,3]]
+    "schur_exp_trans": ({"A": ([1, 3, 2, 4], 2, 2), "B": ([2, 2, 2, 2], 2, 2),
+                         "C": ([0, 0, 0, 0], 2, 2), "D": ([0, 2, 1, 3], 2, 2)},
+                        [5.5, 8.5, 5.5, 8.5]),
+    # (A-B)^2 summed: 9 + 16
+    "sqdiff_accu": ({"A": ([1, 2], 2, 1), "B": ([4, 6], 2, 1)}, [25.0]),
+    # X%Y + sqrt(|W|)/(1 + exp(-V)): 6 + 4/2, 1 + 3/2
+    "schur_sqrt_sigmoid": ({"X": ([2, 1], 2, 1), "Y": ([3, 1], 2, 1), "W": ([-16, 9], 2, 1),
+                            "V": ([0, 0], 2, 1)}, [8.0, 2.5]),
+    # column sums of [[1,2],[6,8]]
+    "schur_colsum": ({"X": ([1, 3, 2, 4], 2, 2), "Y": ([1, 2, 1, 2], 2, 2)}, [7.0, 10.0]),
+    # row maxima of |[[3,4],[1,7]] - [[2,-1],[-1,4]]| = [[1,5],[2,3]] (column maxima
+    # would be 2, 5)
+    "absdiff_rowmax": ({"X": ([3, 1, 4, 7], 2, 2), "Y": ([2, -1, -1, 4], 2, 2)}, [5.0, 3.0]),
+    # |(3, 4)| = 5
+    "diff_norm": ({"X": ([5, 5], 2, 1), "Y": ([2, 1], 2, 1)}, [5.0]),
+    # A%B + 0.5*C^T: [[1,2],[3,4]] + [[1,3],[2,4]]
+    "schur_trans_accu": ({"A": ([1, 3, 2, 4], 2, 2), "B": ([1, 1, 1, 1], 2, 2),
+                          "C": ([2, 6, 4, 8], 2, 2)}, [2.0, 5.0, 5.0, 8.0]),
+    # X%W = 0, so sigmoid(b_r) = 1/2 (row 0), 3/4 (row 1); residuals 0, .5, 0, -.25
+    "sigmoid_sqloss": ({"X": ([0, 0, 0, 0], 2, 2), "W": ([7, -3, 2, 5], 2, 2),
+                        "Y": ([0.5, 0.75, 0, 1], 2, 2), "b": ([0, L3], 2, 1)}, [0.3125]),
+    # 2*(X^T + Y) + 2*(X + Y^T) with X = [[1,2],[3,4]], Y = [[0,1],[1,0]]
+    "expr1": ({"X": ([1, 3, 2, 4], 2, 2), "Y": ([0, 1, 1, 0], 2, 2)}, [4.0, 14.0, 14.0, 16.0]),
+    "relu": ({"X": ([-2, 0, 3.5, -0.25], 2, 2)}, [0.0, 0.0, 3.5, 0.0]),
+    "sigmoid": ({"X": ([0, L3, -L3], 3, 1)}, [0.5, 0.75, 0.25]),
+    # (1 + 2) * (3 + 4)
+    "sum_schur": ({"A": ([1], 1, 1), "B": ([2], 1, 1), "C": ([3], 1, 1), "D": ([4], 1, 1)},
+                  [21.0]),
+    # 2 * X Y^T, X = [[1,2],[3,4]], Y = [[1,2],[0,1]]: X Y^T = [[5,2],[11,4]]
+    # (X Y would be [[1,4],[3,10]])
+    "gemm_scale": ({"X": ([1, 3, 2, 4], 2, 2), "Y": ([1, 0, 2, 1], 2, 2)},
+                   [10.0, 22.0, 4.0, 8.0]),
+    # sigmoid(0.5 X Y + W), X = [[2,2],[0,2]], Y = [[1,0],[-1,1]]: 0.5 X Y =
+    # [[0,1],[-1,1]] (0.5 Y X would be [[1,1],[-1,0]]); + W = [[0, ln3], [-ln3, 0]]
+    "gemm_epilogue": ({"X": ([2, 0, 2, 2], 2, 2), "Y": ([1, -1, 0, 1], 2, 2),
+                       "W": ([0, 1 - L3, L3 - 1, -1], 2, 2)}, [0.5, 0.25, 0.75, 0.5]),
+    # [[1,1],[0,1]] [[1,0],[1,1]] = [[2,1],[1,1]]; * [[0,1],[1,0]] = [[1,2],[1,1]];
+    # * diag(1, 2) = [[1,4],[1,2]]
+    "chain": ({"A": ([1, 0, 1, 1], 2, 2), "B": ([1, 1, 0, 1], 2, 2), "C": ([0, 1, 1, 0], 2, 2),
+               "D": ([1, 0, 0, 2], 2, 2)}, [1.0, 1.0, 4.0, 2.0]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(HAND_TREES))
+def test_suite_trees_by_hand(name):
+    from harness import tree_of
+    leaves, want = HAND_TREES[name]
+    env = {k: buf(v, r, c) for k, (v, r, c) in leaves.items()}
+    got = np.asarray(oracle.evaluate(tree_of(name), env), dtype=np.float64)
+    got = got.T.ravel() if got.ndim == 2 else got.ravel()
+    assert np.allclose(got, want, rtol=0, atol=1e-15), (name, got, want)
+
+
+@pytest.mark.parametrize("n", range(2, 17))
+def test_add_n_of_index_matrices(n):
+    """add-N over A_k = k * ones sums to n(n+1)/2 everywhere."""
+    from harness import tree_of
+    env = {f"A{k}": buf([float(k)] * 6, 2, 3) for k in range(1, n + 1)}
+    got = oracle.evaluate(tree_of(f"add{n}"), env)
+    assert np.all(got == n * (n + 1) / 2)
