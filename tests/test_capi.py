@@ -169,3 +169,24 @@ def test_product_trees_listed(fxlib):
         fxlib.fx_expr_destroy(h)
     h = fxlib.fx_expr_create("chain", fxlib.FX_F32)
     fxlib.fx_expr_destroy(h)
+
+
+def test_launch_shape_validation(fxlib):
+    """fx_expr_set_launch_shape accepts the documented ranges (block 64-512
+    in warps, unroll 2/4/8, blocks per SM 0-32, pipeline 0-2), rejects the rest
+    without changing the shape in force, and reads back what it set."""
+    h = fxlib.fx_expr_create("schur_sqrt_sigmoid", fxlib.FX_F32)
+    try:
+        assert fxlib.fx_expr_launch_shape(h) == (256, 4, 0, 0)
+        for good in [(64, 2, 0, 0), (512, 8, 32, 2), (96, 4, 1, 1), (256, 2, 4, 2)]:
+            fxlib.fx_expr_set_launch_shape(h, *good)
+            assert fxlib.fx_expr_launch_shape(h) == good
+        before = fxlib.fx_expr_launch_shape(h)
+        for bad in [(48, 4, 0, 0), (100, 4, 0, 0), (544, 4, 0, 0), (256, 1, 0, 0), (256, 3, 0, 0),
+                    (256, 16, 0, 0), (256, 4, -1, 0), (256, 4, 33, 0), (256, 4, 0, -1),
+                    (256, 4, 0, 3)]:
+            with pytest.raises(fxlib.FxError):
+                fxlib.fx_expr_set_launch_shape(h, *bad)
+            assert fxlib.fx_expr_launch_shape(h) == before
+    finally:
+        fxlib.fx_expr_destroy(h)
