@@ -173,6 +173,9 @@ fx_status fx_eval_host(fx_expr* x, const void* const* host_in, void* const* host
  * With use_graph != 0 the two launches are captured in a CUDA graph the
  * first time a given items array (same contents) is seen and replayed
  * afterwards. The item array is read on the host during the call only.
+ * Every matrix operand of an item (inputs and Z) must span fewer than 2^31
+ * elements (ld * (cols - 1) + rows), since the batched kernel addresses a
+ * matrix with 32-bit offsets: FX_E_SHAPE otherwise, before any launch.
  * FX_E_UNSUPPORTED for trees without a batched entry. */
 fx_status fx_eval_batch(fx_expr* x, int64_t n, const fx_batch_item* items, void* stream,
                         int use_graph);

@@ -414,6 +414,31 @@ bool batch_leaf_check(const fx_batch_item& it, int64_t R, int64_t C, bool& vec, 
   return true;
 }
 
+// The batched kernel addresses a matrix's elements with 32-bit offsets
+// (column * ld + row inside a tile, 32-bit tile indices): every matrix
+// operand of an item must span fewer than 2^31 elements.
+constexpr int64_t kBatchSpan = int64_t(1) << 31;
+inline bool batch_span_ok(int64_t rows, int64_t cols, int64_t ld) {
+  return rows * cols == 0 || (ld < kBatchSpan && ld * (cols - 1) + rows < kBatchSpan);
+}
+template <class LL, int I = 0>
+bool batch_extent_check(const fx_batch_item& it, int64_t R, int64_t C, int& bad) {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    const int k = L::slot;
+    if constexpr (L::mode == MN || L::mode == MT) {
+      const int64_t rows = L::mode == MT ? C : R, cols = L::mode == MT ? R : C;
+      const int64_t ld = it.ld[k] ? it.ld[k] : (rows > 0 ? rows : 1);
+      if (!batch_span_ok(rows, cols, ld)) {
+        bad = k;
+        return false;
+      }
+    }
+    return batch_extent_check<LL, I + 1>(it, R, C, bad);
+  }
+  return true;
+}
+
 // Plain leaves of a batch matrix: one leading dimension, one base alignment
 // modulo `align` bytes? `first` receives the first plain leaf's slot.
 template <class LL, int I = 0> bool skew_check(const BatchMat& m, int& first, int align) {
@@ -490,12 +515,15 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
         const fx_batch_item& it = items[i];
         const int64_t R = it.rows, C = it.cols;
         if (R < 0 || C < 0) return fail(FX_E_SHAPE, "item %lld: negative shape", (long long)i);
-        if (R > (int64_t(1) << 31) || C > (int64_t(1) << 31))
+        if (R >= kBatchSpan || C >= kBatchSpan)
           return fail(FX_E_SHAPE, "item %lld: too large for a batch", (long long)i);
         bool vec = true;
         int bad = -1;
         if (!batch_leaf_check<LL, V>(it, R, C, vec, bad))
           return fail(FX_E_ARG, "item %lld: slot %d has a bad pointer or ld", (long long)i, bad);
+        if (!batch_extent_check<LL>(it, R, C, bad))
+          return fail(FX_E_SHAPE, "item %lld: slot %d spans 2^31 elements or more (batch limit)",
+                      (long long)i, bad);
         BatchMat& m = mats[i];
         memset(&m, 0, sizeof m);
         for (int k = 0; k < n_in; ++k) {
@@ -507,6 +535,9 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
           const int64_t ldz = it.ld[zs] ? it.ld[zs] : (R > 0 ? R : 1);
           if (ldz < R || (R * C > 0 && !it.ptr[zs]) || !aligned(it.ptr[zs], sizeof(T)))
             return fail(FX_E_ARG, "item %lld: bad output Z", (long long)i);
+          if (!batch_span_ok(R, C, ldz))
+            return fail(FX_E_SHAPE, "item %lld: Z spans 2^31 elements or more (batch limit)",
+                        (long long)i);
           m.p[zs] = it.ptr[zs];
           m.ld[zs] = ldz;
           if (!aligned(it.ptr[zs], sizeof(T) * V) || ldz % V != 0) vec = false;

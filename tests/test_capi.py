@@ -190,3 +190,31 @@ def test_launch_shape_validation(fxlib):
             assert fxlib.fx_expr_launch_shape(h) == before
     finally:
         fxlib.fx_expr_destroy(h)
+
+
+def test_batch_rejects_operands_beyond_32bit_offsets(fxlib):
+    """fx_eval_batch refuses, on the host and before any launch, items whose
+    matrix operands span 2^31 elements or more (the batched kernel's 32-bit
+    offsets); the pointers are never dereferenced."""
+    FX_E_SHAPE = -2
+    h = fxlib.fx_expr_create("schur_trans_accu", fxlib.FX_F32)   # A, B, C (transposed), Z, s
+    try:
+        def item(R, C, ld=None):
+            it = (fxlib.BatchItem * 1)()
+            for k in range(5):
+                it[0].ptr[k] = 0x10000000 + k * 0x1000000
+            for k, v in (ld or {}).items():
+                it[0].ld[k] = v
+            it[0].rows, it[0].cols = R, C
+            return it
+        cases = [item(1 << 16, 1 << 16),                 # 2^32 elements
+                 item(1000, 1000, {0: 1 << 22}),         # A's leading dimension
+                 item(1000, 1000, {2: 1 << 22}),         # the transposed C (cols x rows)
+                 item(1000, 1000, {3: 1 << 22}),         # Z
+                 item(1 << 31, 1)]                       # rows beyond int32
+        for it in cases:
+            with pytest.raises(fxlib.FxError) as e:
+                fxlib.fx_eval_batch(h, it, 0, True)
+            assert e.value.status == FX_E_SHAPE, fxlib.fx_last_error_string()
+    finally:
+        fxlib.fx_expr_destroy(h)
