@@ -24,6 +24,16 @@ no flush between iterations.
   suite10k       the Sec. 4 expressions at 10000^2 FP32: add-N, N = 2..16,
                  expr1, expr2, relu, sigmoid, swish, gelu
 
+  prec16384_f16_clamped   prec16384_f16's Z with C's values capped at 9 (every
+                 FP16 output finite)
+
+With no flags, the line also carries "errors" (every output of the step
+against the FP64 oracle, after the timed region) and "configs": each of
+small1024, expr8192_f64, prec16384_bf16, prec16384_f16,
+prec16384_f16_clamped, batch4096, loss8192_f32 and loss8192_bf16 measured
+the same way (autotuned, --config-steps timed steps), with its GB/s,
+roofline fraction, speedup over the unfused baseline and errors.
+
 --gpus N: N independent replicas (one process per GPU, torch.distributed.run);
 value = bytes of all ranks / max elapsed time over ranks.
 --impl reference: the FP64 CPU oracle, timed on a bounded sample of the
@@ -204,6 +214,8 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
             _bind(fx, h, len(ins), o, R, 1, R)
             nb += R * rs
         keep[key] = (h, o)
+        keep.setdefault("_handles", []).append(h)
+        keep.setdefault("trees", []).append((name, key, list(ins), kind))
         ops.append(Op(key, nb, (lambda h=h: fx.fx_eval(h, sp)),
                       (lambda h=h: fx.fx_eval_unfused(h, sp)),
                       (lambda h=h: fx.fx_expr_last_launches(h))))
@@ -227,16 +239,26 @@ def workload(name, fx, torch, dev, sp, keep, size=8192, count=4096):
                "l2": "inputs larger than L2 (256 MiB each in FP32), no flush"}
         keep["env"] = env
         return _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep), cfg, "Z", False, storage
-    if name in ("small1024", "prec16384_bf16", "prec16384_f16"):
+    if name in ("small1024", "prec16384_bf16", "prec16384_f16", "prec16384_f16_clamped"):
         storage = "f32" if name == "small1024" else name.split("_")[1]
         R = C = (1024 if name == "small1024" else 16384) if size == 8192 else size
         dist = "uniform" if name == "small1024" else "lognormal_signed"
         env = synth.operands(0, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], storage, dist)
+        inputs = f"A,B,C,D {dist}, seed 0, column-major"
         trees = [("schur_exp_trans", "Z", "ABCD", "Z"), ("sqdiff_accu", "s", "AB", "s")]
+        if name.endswith("_clamped"):
+            # C's values capped at 9: 3.5 exp(9) = 28361 stays finite in FP16
+            c = env["C"]
+            cap = synth.round_to_storage(np.array([9.0]), storage)[0]
+            env["C"] = synth.Buffer(np.where(synth.to_f64(c.data, storage) > 9.0, cap, c.data),
+                                    c.rows, c.cols, c.ld, storage)
+            inputs += "; C capped at 9"
+            trees = trees[:1]
         cfg = {"workload": f"A%B+3.5*exp(C)-trans(D) and accu(square(A-B)) at {R}x{C}",
-               "rows": R, "cols": C, "inputs": f"A,B,C,D {dist}, seed 0, column-major",
+               "rows": R, "cols": C, "inputs": inputs,
                "l2": "L2 flushed before every kernel (256 MiB write), device-timed per kernel"
                if name == "small1024" else "inputs larger than L2, no flush"}
+        keep["env"] = env
         return (_expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep), cfg, "Z",
                 name == "small1024", storage)
     if name == "batch4096":
@@ -258,6 +280,7 @@ def workload(name, fx, torch, dev, sp, keep, size=8192, count=4096):
                "inputs": "A1..A16 U[-1,1], seed 4; P1, P2 U[0.5,2], seed 5; Y64 FP64 N(0,1), "
                          "seed 6; column-major",
                "l2": "inputs larger than L2 (400 MB each), no flush"}
+        keep["env"] = env
         return _expr_ops(fx, torch, dev, sp, trees, "f32", env, R, C, keep), cfg, "add16", False, "f32"
     if name in ("loss8192_f32", "loss8192_bf16"):
         return loss_workload(fx, torch, dev, sp, keep, name.split("_")[1], size)
@@ -283,6 +306,12 @@ def batch_workload(fx, torch, dev, sp, keep, count=4096):
     A, oa = arena(ops_["A"])
     B, ob = arena(ops_["B"])
     Cm, oc = arena(ops_["C"])
+    # 64 matrices (seeded) plus the largest and the smallest are kept for the
+    # oracle check after the timed region
+    rng = np.random.default_rng(2)
+    pick = sorted(set(rng.choice(n, 64, replace=False).tolist()) |
+                  {int(np.argmax(rows * cols)), int(np.argmin(rows * cols))})
+    keep["batch_sample"] = (pick, {k: [ops_[k][i] for i in pick] for k in "ABC"})
     del ops_
     oz, pos = [], 0
     for r, c in zip(rows, cols):
@@ -301,6 +330,8 @@ def batch_workload(fx, torch, dev, sp, keep, count=4096):
         it.rows, it.cols = int(rows[i]), int(cols[i])
     h = fx.fx_expr_create("schur_trans_accu", fx.FX_F32)
     keep["batch"] = (A, B, Cm, Z, S, items, h)
+    keep["batch_offsets"] = (oz, rows, cols)
+    keep.setdefault("_handles", []).append(h)
     nel = int(np.sum(rows * cols))
     nbytes = 16 * nel + 4 * n
     # unfused and unbatched baseline: the same tree one operator per launch, matrix by matrix
@@ -315,6 +346,7 @@ def batch_workload(fx, torch, dev, sp, keep, count=4096):
         fx.fx_expr_bind(e, 4, items[i].ptr[4], 1, 1, 1)
         per.append(e)
     keep["per"] = per
+    keep["_handles"].extend(per)
 
     def unfused():
         for e in per:
@@ -352,6 +384,8 @@ def loss_workload(fx, torch, dev, sp, keep, storage, size=8192):
     g["b"] = torch.empty(R, dtype=tdt, device=dev)
     ptrs = [g["X"].data_ptr(), g["W"].data_ptr(), 0, g["b"].data_ptr()]
     keep["loss"] = (d, L, g, h)
+    keep["env"] = env
+    keep.setdefault("_handles", []).append(h)
     fwd_bytes = 3 * R * C * es + R * es + 4
     bwd_bytes = 3 * R * C * es + R * es + 2 * R * C * es + R * es
     ops = [Op("forward", fwd_bytes, lambda: fx.fx_eval(h, sp), lambda: fx.fx_eval_unfused(h, sp),
@@ -454,7 +488,295 @@ def run_reference(args, rank, world):
         "gpu_launches": 0}), flush=True)
 
 
+# ---------------------------------------------------------------- oracle check leg
+#
+# After the timed region, each output of a step is compared with the FP64
+# oracle (the checker: nothing here is timed, and no result of the library
+# is computed by it). Element-wise outputs are compared at 2^16 seeded
+# positions, reductions in full, the batch on 66 whole matrices, the
+# gradients on 16 whole rows. Each entry carries the maximum scaled error
+# under the oracle's running error bound sigma and under its magnitude
+# scale m, the maximum plain relative error, the tolerance and the scale it
+# gates on, and the counts of wrong non-finite outputs and of outputs that
+# are expected to overflow the storage type.
+
+# oracle trees of the compiled trees, over the workloads' input names
+ORACLE_OF = {
+    "schur_sqrt_sigmoid": "(+ (% X Y) (/ (sqrt (abs W)) (+ 1.0 (exp (neg V)))))",
+    "schur_colsum": "(sum (% X Y) 0)",
+    "absdiff_rowmax": "(max (abs (- X Y)) 1)",
+    "diff_norm": "(norm (- X Y))",
+    "schur_exp_trans": "(- (+ (% A B) (* 3.5 (exp C))) (t D))",
+    "sqdiff_accu": "(accu (square (- A B)))",
+    "schur_trans_accu": "(+ (% A B) (* 0.5 (t C)))",
+    "sigmoid_sqloss": "(accu (square (- (sigmoid (+ (% X W) (each_col b))) Y)))",
+}
+
+
+def _host64(t):
+    import torch
+    return t.detach().to(torch.float64).cpu().numpy()
+
+
+def oracle_errors(keep, storage, n_sample=1 << 16):
+    """{output key: error summary} for the outputs kept by a workload."""
+    import concurrent.futures as cf
+
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import grad as ograd
+    from oracle.compare import TOL_TRANS, ErrorReport, gate_scale, tolerance
+
+    rst = "f64" if storage == "f64" else "f32"      # reductions come out in FP32 / FP64
+    jobs = {}
+    env = keep.get("env")
+    for name, key, ins, kind in keep.get("trees", []):
+        tree = ORACLE_OF[name]
+        _, o = keep[key]
+        if kind == "Z":
+            first = env[ins[0]]
+            R, C = first.rows, first.cols
+            rng = np.random.default_rng(99)
+            rr = rng.integers(0, R, n_sample)
+            cc = rng.integers(0, C, n_sample)
+            g = _host64(o[torch.from_numpy(rr + cc * R).to(o.device)])
+
+            def zjob(tree=tree, rr=rr, cc=cc, g=g):
+                v, sg = oracle.at_sigma(tree, env, rr, cc)
+                m = oracle.at_mag(tree, env, rr, cc)
+                return ErrorReport(storage, tolerance(tree, storage), gate_scale(tree)).add(
+                    g, v, sg, m)
+            jobs[key] = zjob
+        else:
+            g = _host64(o).ravel()
+
+            def rjob(tree=tree, g=g):
+                v, sg = oracle.evaluate_sigma(tree, env)
+                m = oracle.evaluate_mag(tree, env)
+                return ErrorReport(rst, tolerance(tree, storage), gate_scale(tree)).add(
+                    g, v.ravel(), sg.ravel(), m.ravel())
+            jobs[key] = rjob
+    if "loss" in keep:
+        tree = ORACLE_OF["sigmoid_sqloss"]
+        _, L, grads, _ = keep["loss"]
+        lv = _host64(L)
+
+        def fjob():
+            v, sg = oracle.evaluate_sigma(tree, env)
+            m = oracle.evaluate_mag(tree, env)
+            return ErrorReport("f32", tolerance(tree, storage), gate_scale(tree)).add(
+                lv, v.ravel(), sg.ravel(), m.ravel())
+        jobs["forward"] = fjob
+        R = env["X"].rows
+        rows = np.sort(np.random.default_rng(3).choice(R, 16, replace=False))
+        ghost = {k: t for k, t in grads.items()}
+
+        def bjob():
+            ref = ograd.gradient_sigma(tree, env, 1.0, rows=rows)
+            # gradients are element-wise outputs of the reverse pass, stored
+            # in the storage type and held to its bound through sigmoid
+            rep = ErrorReport(storage, TOL_TRANS[storage], "sigma")
+            for s_, (idx, v, sg) in ref.items():
+                if s_ in ghost:
+                    g = _host64(ghost[s_][torch.from_numpy(idx).to(ghost[s_].device)])
+                    rep.add(g, v, sg)
+            return rep
+        jobs["backward"] = bjob
+    if "batch" in keep:
+        tree = ORACLE_OF["schur_trans_accu"]
+        pick, mats = keep["batch_sample"]
+        _, _, _, Z, S, _, _ = keep["batch"]
+        oz, rows, cols = keep["batch_offsets"]
+        Sh = _host64(S)
+        zs = {}
+        for j, i in enumerate(pick):
+            r, c = int(rows[i]), int(cols[i])
+            zs[i] = _host64(Z[oz[i]:oz[i] + r * c]).reshape(c, r).T
+
+        def bzjob():
+            rep = ErrorReport("f32", tolerance(tree, "f32"), gate_scale(tree))
+            for j, i in enumerate(pick):
+                e = {k: mats[k][j] for k in "ABC"}
+                v, sg = oracle.evaluate_sigma(tree, e)
+                rep.add(zs[i], v, sg, oracle.evaluate_mag(tree, e))
+            return rep
+
+        def bsjob():
+            t = f"(accu {tree})"
+            rep = ErrorReport("f32", tolerance(t, "f32"), gate_scale(t))
+            for j, i in enumerate(pick):
+                e = {k: mats[k][j] for k in "ABC"}
+                v, sg = oracle.evaluate_sigma(t, e)
+                rep.add([Sh[i]], v.ravel(), sg.ravel(), oracle.evaluate_mag(t, e).ravel())
+            return rep
+        jobs["batch_Z"] = bzjob
+        jobs["batch_s"] = bsjob
+    out = {}
+    with cf.ThreadPoolExecutor(max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        futs = {k: ex.submit(f) for k, f in jobs.items()}
+        for k, f in futs.items():
+            d = f.result().as_dict()
+            d["ok"] = (d["nonfinite"] == 0 and
+                       (d["max_scaled_err_m"] if d["gate"] == "m" else
+                        d["max_scaled_err_sigma"]) <= d["tol"])
+            out[k] = d
+    return out
+
+
 # ---------------------------------------------------------------- GPU run
+
+def tune_workload(fx, args, keep, ops, cfg, sp):
+    """Launch shapes: fixed by --shape, else every tree autotuned (fx_tune
+    search; the unfused baseline keeps the library's default shapes), and the
+    batch by fx_tune_batch. Returns the expression handles by op key."""
+    keys = [o.key for o in ops]
+    handles = {key: val[0] for key, val in keep.items()
+               if isinstance(val, tuple) and len(val) == 2 and key in keys}
+    if "loss" in keep:
+        handles["loss"] = keep["loss"][3]
+    if args.shape:
+        cfg["launch_shape"] = args.shape
+        for h in handles.values():
+            fx.fx_expr_set_launch_shape(h, *[int(v) for v in args.shape.split(",")])
+    elif not args.no_tune and handles:
+        for h in handles.values():
+            fx.fx_tune(h, "search", sp)
+        cfg["launch_shape"] = {k: "autotuned: block %d, unroll %d, blocks/SM %d, pipeline %d"
+                               % tuple(fx.fx_expr_launch_shape(h)) for k, h in handles.items()}
+    if "batch" in keep:
+        hb, items = keep["batch"][6], keep["batch"][5]
+        fx.fx_tune_batch(hb, items, "search", sp)
+        cfg["launch_shape"] = "autotuned: block %d, unroll %d, blocks/SM %d, pipeline %d" % tuple(
+            fx.fx_expr_launch_shape(hb))
+    return handles
+
+
+def timed_steps(torch, stream, ops, K, W, fl, before=None, after=None):
+    """W untimed steps, then exactly K timed steps on `stream`: per-op
+    CUDA-event times (ms) of every launch, the whole region's device time
+    (ms), the kernel launches counted and the host wall-clock bounds of the
+    region. `before`/`after` run around the region (clocks, barriers)."""
+    for _ in range(W):
+        for o in ops:
+            fl()
+            o.launch()
+    torch.cuda.synchronize()
+    ev = {o.key: [] for o in ops}
+    if before:
+        before()
+    torch.cuda.synchronize()
+    t_start = time.time()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    launches = 0
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
+    for _ in range(K):
+        for o in ops:
+            fl()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            o.launch()
+            b.record(stream)
+            ev[o.key].append((a, b))
+            launches += o.launches() if o.launches else 1
+    t1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    t_end = time.time()
+    if after:
+        after()
+    per_all = {k: [a.elapsed_time(b) for a, b in v] for k, v in ev.items()}
+    return per_all, t0.elapsed_time(t1), launches, t_start, t_end
+
+
+def unfused_steps(torch, stream, ops, K, fl):
+    """Mean CUDA-event time (ms) of the unfused baseline of every op that has one."""
+    uops = [o for o in ops if o.unfused]
+    uk = max(3, min(K, 20))
+    for o in uops:
+        o.unfused()
+    torch.cuda.synchronize()
+    uev = {o.key: [] for o in uops}
+    for _ in range(uk):
+        for o in uops:
+            fl()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            o.unfused()
+            b.record(stream)
+            uev[o.key].append((a, b))
+    torch.cuda.synchronize()
+    return {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in uev.items()}
+
+
+def release(fx, torch, keep):
+    """Frees a workload's expression objects and device buffers."""
+    torch.cuda.synchronize()
+    for h in keep.get("_handles", []):
+        fx.fx_expr_destroy(h)
+    keep.clear()
+    torch.cuda.empty_cache()
+
+
+# the other measured configurations, reported in the default line's "configs"
+EXTRA_CONFIGS = ["small1024", "expr8192_f64", "prec16384_bf16", "prec16384_f16",
+                 "prec16384_f16_clamped", "batch4096", "loss8192_f32", "loss8192_bf16"]
+
+
+def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
+    """One configuration measured as the default line is (autotuned, K timed
+    steps after W warm-up steps, CUDA events), its unfused baseline, and its
+    outputs' errors against the oracle (after the timed region)."""
+    keep = {}
+    ops, cfg, dom, flush, storage = workload(name, fx, torch, dev, sp, keep, 8192, args.count)
+    try:
+        handles = tune_workload(fx, args, keep, ops, cfg, sp)
+        flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
+
+        def fl():
+            if flush_buf is not None:
+                flush_buf.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            per_all, ms, launches, _, _ = timed_steps(torch, stream, ops, K, W, fl)
+            u_ms = unfused_steps(torch, stream, ops, K, fl)
+        per_ms = {k: statistics.mean(v) for k, v in per_all.items()}
+        if flush:
+            ms = K * sum(per_ms.values())
+        step_bytes = sum(o.bytes for o in ops)
+        dom_op = next(o for o in ops if o.key == dom)
+        dom_gbs = dom_op.bytes / per_ms[dom] / 1e6
+        fused_u = sum(per_ms[k] for k in u_ms)
+        out = {
+            "workload": cfg["workload"], "dtype": storage, "steps": K, "warmup": W,
+            "value": round(step_bytes * K / (ms / 1e3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms / K, 4), "pct_of_peak": round(100 * step_bytes * K / (ms / 1e3) / 1e9 / peak, 2),
+            "vs_unfused": round(sum(u_ms.values()) / fused_u, 3) if u_ms else None,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(dom_gbs, 2),
+                         "peak": peak, "unit": "GB/s", "frac": round(dom_gbs / peak, 4),
+                         "alg_bytes_per_launch": dom_op.bytes,
+                         "avg_launch_ms": round(per_ms[dom], 4)},
+            "per_op": {k: {"ms": round(per_ms[k], 4), "bytes": next(o.bytes for o in ops if o.key == k),
+                           "gbs": round(next(o.bytes for o in ops if o.key == k) / per_ms[k] / 1e6, 1),
+                           "unfused_ms": round(u_ms[k], 4) if k in u_ms else None}
+                       for k in per_ms},
+            "gpu_launches": launches, "launch_shape": cfg.get("launch_shape"), "l2": cfg["l2"],
+            "inputs": cfg.get("inputs"),
+        }
+        if (name, dom) in FP64_PIPE_OPS:
+            alu = fp64_roofline(fx, sp, name, dom, dom_op, per_ms[dom], peak, storage, cfg)
+            if alu:
+                out["roofline_alu"] = alu
+        out["errors"] = oracle_errors(keep, storage)
+        return out
+    finally:
+        release(fx, torch, keep)
+
 
 def run_ours(args, rank, world):
     import torch
@@ -470,27 +792,7 @@ def run_ours(args, rank, world):
     keep = {}
     ops, cfg, dom, flush, storage = workload(args.workload, fx, torch, dev, sp, keep, args.size,
                                             args.count)
-    handles = {key: val[0] for key, val in keep.items()
-               if isinstance(val, tuple) and len(val) == 2 and key in [o.key for o in ops]}
-    if "loss" in keep:
-        handles["loss"] = keep["loss"][3]
-    if args.shape:
-        cfg["launch_shape"] = args.shape
-        for h in handles.values():
-            fx.fx_expr_set_launch_shape(h, *[int(v) for v in args.shape.split(",")])
-    elif not args.no_tune and handles:
-        # every tree's launch shape autotuned before the timed region (the
-        # unfused baseline keeps the library's default shapes)
-        for h in handles.values():
-            fx.fx_tune(h, "search", sp)
-        cfg["launch_shape"] = {k: "autotuned: block %d, unroll %d, blocks/SM %d, pipeline %d"
-                               % tuple(fx.fx_expr_launch_shape(h)) for k, h in handles.items()}
-    if "batch" in keep:
-        # the batched workload is autotuned (block size, stages, residency)
-        hb, items = keep["batch"][6], keep["batch"][5]
-        fx.fx_tune_batch(hb, items, "search", sp)
-        cfg["launch_shape"] = "autotuned: block %d, unroll %d, blocks/SM %d, pipeline %d" % tuple(
-            fx.fx_expr_launch_shape(hb))
+    handles = tune_workload(fx, args, keep, ops, cfg, sp)
     flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
     torch.cuda.synchronize()
     step_bytes = sum(o.bytes for o in ops)
@@ -500,66 +802,27 @@ def run_ours(args, rank, world):
         if flush_buf is not None:
             flush_buf.zero_()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            for o in ops:
-                fl()
-                o.launch()
-        torch.cuda.synchronize()
-        ev = {o.key: [] for o in ops}
-        clk = Clocks(local)
+    clk = Clocks(local)
+
+    def before():
         clk.start()
         time.sleep(0.4)
         if world > 1:
             dist.barrier()
-        torch.cuda.synchronize()
-        t_start = time.time()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        launches = 0
-        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
-        for i in range(K):
-            for o in ops:
-                fl()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                o.launch()
-                b.record(stream)
-                ev[o.key].append((a, b))
-                launches += o.launches() if o.launches else 1
-        t1.record(stream)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        t_end = time.time()
+
+    def after():
         if world > 1:
             dist.barrier()
+
+    with torch.cuda.stream(stream):
+        per_all, ms, launches, t_start, t_end = timed_steps(torch, stream, ops, K, args.warmup, fl,
+                                                            before, after)
         clocks = clk.stop(t_start, t_end)
-        per_all = {k: [a.elapsed_time(b) for a, b in v] for k, v in ev.items()}
         per_ms = {k: statistics.mean(v) for k, v in per_all.items()}
-        ms = t0.elapsed_time(t1)
         if flush:   # device time of the kernels alone (flushes excluded)
             ms = K * sum(per_ms.values())
-
         # unfused baseline: the same step, one kernel per operator
-        uops = [o for o in ops if o.unfused]
-        uk = max(3, min(K, 20))
-        for o in uops:
-            o.unfused()
-        torch.cuda.synchronize()
-        uev = {o.key: [] for o in uops}
-        for _ in range(uk):
-            for o in uops:
-                fl()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                o.unfused()
-                b.record(stream)
-                uev[o.key].append((a, b))
-        torch.cuda.synchronize()
-        u_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in uev.items()}
+        u_ms = unfused_steps(torch, stream, ops, K, fl)
         e2e = None
         if args.workload in ("expr8192", "expr8192_f64"):
             e2e = e2e_run(fx, torch, stream, sp, keep, storage, K, args.size)
@@ -620,6 +883,14 @@ def run_ours(args, rank, world):
             line["roofline"] = alu
     if e2e:
         line["e2e"] = e2e
+    if not args.no_check:
+        line["errors"] = oracle_errors(keep, storage)
+    if world == 1 and args.workload == "expr8192" and args.size == 8192 and not args.no_configs:
+        release(fx, torch, keep)
+        line["configs"] = {}
+        for name in EXTRA_CONFIGS:
+            line["configs"][name] = run_config(args, name, fx, torch, dev, stream, sp, peak,
+                                               args.config_steps, 3)
     print(json.dumps(line), flush=True)
 
 
@@ -692,8 +963,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="expr8192",
                     choices=["expr8192", "expr8192_f64", "small1024", "prec16384_bf16",
-                             "prec16384_f16", "batch4096", "loss8192_f32", "loss8192_bf16",
-                             "suite10k"])
+                             "prec16384_f16", "prec16384_f16_clamped", "batch4096",
+                             "loss8192_f32", "loss8192_bf16", "suite10k"])
     ap.add_argument("--size", type=int, default=8192,
                     help="rows = cols of the expr8192 and loss8192 workloads (other values than "
                          "8192 also resize prec16384_* and suite10k, for profiling)")
@@ -703,6 +974,12 @@ def main():
     ap.add_argument("--shape", default="",
                     help="fixed launch shape block,unroll,blocks_per_sm,pipeline for every tree")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-check", action="store_true",
+                    help="skip the comparison of the outputs with the oracle")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only: skip the other configurations' entries")
+    ap.add_argument("--config-steps", type=int, default=10,
+                    help="timed steps of each other configuration in the default line")
     ap.add_argument("--cpu-cols", type=int, default=4096)
     ap.add_argument("--ref-cols", type=int, default=512)
     args = ap.parse_args()

@@ -8,7 +8,8 @@
  * the tree is a compile-time C++ type (Sec. 3, the AST-as-type paragraph),
  * instantiated at build time into kernels, so that the expression is computed
  * in one pass over its input matrices (Sec. 5). Expressions are therefore
- * chosen by name from the set compiled into the library (fx_list_exprs).
+ * chosen by name from the set compiled into the library (fx_list_count and
+ * fx_list_get).
  *
  * Conventions that hold for every call:
  *  - Matrices are column-major: element (r, c) is ptr[r + c*ld] (Sec. 3, the
@@ -69,7 +70,9 @@ typedef enum { FX_TUNE_OFF = 0, FX_TUNE_CACHE = 1, FX_TUNE_SEARCH = 2 } fx_tune_
 
 /* One matrix of a batch: a device pointer and leading dimension for every
  * slot (inputs, then outputs), and the shape (rows x cols) of the tree for
- * this matrix. ld[k] == 0 means "contiguous" (the slot's own row count). A
+ * this matrix. ld[k] == 0 means "contiguous" (the slot's own row count); a
+ * leading dimension per slot lets a batch address submatrices of larger
+ * arrays, as fx_expr_bind does for one matrix. A
  * transposed leaf of a rows x cols tree is cols x rows. A scalar output
  * (accu) points to one element. */
 typedef struct {
@@ -103,7 +106,9 @@ fx_status fx_expr_create(const char* name, fx_dtype storage, fx_expr** out);
  * running (synchronise its stream first). NULL is accepted. */
 fx_status fx_expr_destroy(fx_expr* x);
 
-/* Counts of input slots, output slots and scalars, and the root's kind. */
+/* Counts of input slots, output slots and scalars, and the root's kind (the
+ * kind tells a caller which outputs to bind: a matrix, a scalar, a vector,
+ * or a matrix and its sum). */
 fx_status fx_expr_info(const fx_expr* x, int* n_inputs, int* n_outputs, int* n_scalars,
                        fx_kind* kind);
 
@@ -184,14 +189,18 @@ fx_status fx_eval_batch(fx_expr* x, int64_t n, const fx_batch_item* items, void*
  * grad_ptrs[k] != NULL, writes dL/d(input k) scaled by *grad_out into
  * grad_ptrs[k] (device, same shape as input k, dense column-major, storage
  * type). grad_out is a DEVICE pointer to one reduction-type scalar (float,
- * or double for f64), or NULL for 1. The tree is recomputed element by
+ * or double for f64), or NULL for 1: a device pointer rather than a host
+ * value, so that a backward pass queued behind the forward pass and the
+ * caller's own loss arithmetic needs no host synchronisation. The tree is recomputed element by
  * element (no stored intermediates); gradients of broadcast leaves are
  * reduced along the broadcast dimension with the same deterministic
  * combine as fx_eval. FX_E_UNSUPPORTED for other roots. */
 fx_status fx_eval_backward(fx_expr* x, const void* grad_out, void* const* grad_ptrs,
                            void* stream);
 
-/* Autotuner. FX_TUNE_OFF: built-in launch shapes. FX_TUNE_CACHE: use the
+/* Autotuner (it takes the caller's stream, so that its timed trials run in
+ * stream order with the caller's other work). FX_TUNE_OFF: built-in launch
+ * shapes. FX_TUNE_CACHE: use the
  * cached choice for this (expression, storage, shape class, device) if the
  * cache file has one. FX_TUNE_SEARCH: time every candidate launch shape
  * on the currently bound buffers (writes the outputs; synchronises the
@@ -247,7 +256,7 @@ int fx_expr_last_launches(const fx_expr* x);
  * the record is cleared. FX_OK otherwise. */
 fx_status fx_expr_sync_status(fx_expr* x, void* stream);
 
-/* ---- evaluation without device allocation ------------------------------ */
+/* ---- device probes (these allocate and free a small device buffer) ----- */
 
 /* Measured FP64 FMA throughput of the current device in flop/s (two flops
  * per FMA): a short launch of independent FMA chains on every SM, timed
@@ -261,6 +270,8 @@ fx_status fx_fp64_fma_rate(void* stream, double* flops_per_s);
  * the timeout; *word receives the error word (1 = a wait gave up). The
  * kernel always finishes; synchronises `stream`. */
 fx_status fx_selftest_wait_timeout(void* stream, unsigned int* word);
+
+/* ---- evaluation without device allocation ------------------------------ */
 
 /* Bytes of the fixed device array behind fx_sqdiff_accu_f32_noalloc: room
  * for 4096 per-block partial sums (16 bytes each) and a completion ticket. */
@@ -278,16 +289,21 @@ fx_status fx_selftest_wait_timeout(void* stream, unsigned int* word);
  *  - Scratch: a file-scope device array of FX_NOALLOC_SCRATCH bytes, held
  *    by every GPU that loads the library until the process exits.
  *  - The first call on each device looks up that array's device address
- *    (cudaGetSymbolAddress) with the device current; make that first call
- *    before any stream capture on the device.
+ *    (cudaGetSymbolAddress) with the device current and keeps it; make that
+ *    first call before any stream capture on the device. The kept address
+ *    belongs to the device's context: do not call this entry point again
+ *    after cudaDeviceReset in the same process.
  *  - Every call on a device shares the one array, which keeps what the last
  *    call left; the call clears the part that must start at zero. Calls
  *    whose kernels overlap on the GPU (different streams, no ordering) race
  *    on it: order them on one stream or with events.
+ *  - An empty matrix (rows or cols 0) writes 0.
  *  - FX_E_UNSUPPORTED if the launch would need more than 4096 partial sums
  *    (a 152-SM GB300 at the default launch shape needs at most 1216);
  *    FX_E_ARG / FX_E_SHAPE / FX_E_ALIGN as for fx_expr_bind (4-byte
- *    alignment); FX_E_CUDA if a CUDA call fails. Asynchronous on `stream`. */
+ *    alignment), FX_E_SHAPE also for extents whose element indices would
+ *    overflow 64 bits; FX_E_CUDA if a CUDA call fails. Asynchronous on
+ *    `stream`. */
 fx_status fx_sqdiff_accu_f32_noalloc(const float* A, const float* B, int64_t rows, int64_t cols,
                                      int64_t ld, float* s, void* stream);
 

@@ -19,16 +19,18 @@ Compile Time Expression Fusion"):
   ``sum``/``max`` along a dimension and the 2-norm.
 * Reductions use Neumaier-compensated FP64 summation (``sums.py``).
 * ``grad.py``: reverse-mode derivative of ``accu(f(leaves))``.
+* ``compare.py``: the scaled error of a computed result against the oracle's
+  value, scaled by its error bound ``at_sigma`` or magnitude ``at_mag``.
 
 Every value is FP64; inputs are the exact FP64 values of the stored
 (rounded) elements. Sums are the plain mathematical definitions; the only
 freedom is rounding order, which compensated summation makes negligible.
 """
-from .expr import (Node, parse, shape_of, leaves_of, at, at_sigma, evaluate, evaluate_sigma,
-                   REDUCTIONS)
+from .expr import (Node, parse, shape_of, leaves_of, at, at_sigma, at_mag, evaluate,
+                   evaluate_sigma, evaluate_mag, REDUCTIONS)
 from .sums import neumaier, neumaier_axis
 from .grad import local_adjoints, gradient, gradient_rows
 
-__all__ = ["Node", "parse", "shape_of", "leaves_of", "at", "at_sigma", "evaluate",
-           "evaluate_sigma", "REDUCTIONS", "neumaier", "neumaier_axis", "local_adjoints",
+__all__ = ["Node", "parse", "shape_of", "leaves_of", "at", "at_sigma", "at_mag", "evaluate",
+           "evaluate_sigma", "evaluate_mag", "REDUCTIONS", "neumaier", "neumaier_axis", "local_adjoints",
            "gradient", "gradient_rows"]

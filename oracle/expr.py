@@ -390,6 +390,102 @@ def at_sigma(node, env, R, C):
     raise ValueError(f"{op} is not element-wise")
 
 
+def at_mag(node, env, R, C):
+    """Magnitude scale ``m`` at positions ``(R, C)``: the tree evaluated on
+    absolute values, with every sign-dependent step made sign-free.
+
+        m(leaf) = |leaf|           m(number) = |number|
+        m(a +- b) = m(a) + m(b)    m(a % b) = m(a) m(b)   m(a / b) = m(a) / |b|
+        m(f(a)) = |f(m(a))| for the unary functions (neg and abs: m(a))
+        m(pow(a, k)) = m(a)^k      m(gt(a, s)) = gt(a, s) (exact 0 or 1)
+        m(matrix product) = |A| |B| (products of magnitudes, summed)
+        t and broadcasts map positions as the value rule does
+
+    For trees of sums, differences, products, quotients and scalars of
+    exactly stored leaves this is the componentwise condition scale of
+    rounding-error analysis (Higham, Accuracy and Stability of Numerical
+    Algorithms, Sec. 3.1-3.3): evaluating such a tree with unit roundoff u
+    errs by at most about k u m for a small k set by the tree's depth, and
+    m >= |value|. Transcendental nodes carry no such bound (an error in
+    their argument is amplified by the derivative), which is why at_sigma
+    exists; m is the scale for the trees without them.
+    """
+    n = parse(node)
+    op = n.op
+    if op == "num":
+        return abs(n.value)
+    if op == "leaf":
+        return np.abs(_leaf_values(env[n.name], R, C))
+    if op == "t":
+        return at_mag(n.args[0], env, C, R)
+    if op == "each_col":
+        return at_mag(n.args[0], env, R, np.zeros_like(np.asarray(C)))
+    if op == "each_row":
+        return at_mag(n.args[0], env, np.zeros_like(np.asarray(R)), C)
+    if op in UNARY:
+        a = at_mag(n.args[0], env, R, C)
+        if op in _EXACT_UNARY:
+            return a
+        return np.abs(_apply_unary(op, a))
+    if op == "pow":
+        with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+            return np.abs(np.power(at_mag(n.args[0], env, R, C), n.args[1].value))
+    if op == "gt":
+        return at(n, env, R, C)
+    if _is_product(n):
+        A = np.abs(_materialise(n.args[0], env))
+        B = np.abs(_materialise(n.args[1], env))
+        R, C = np.broadcast_arrays(np.asarray(R), np.asarray(C))
+        return (A @ B)[R, C]
+    if op in BINARY:
+        a = at_mag(n.args[0], env, R, C)
+        b = at_mag(n.args[1], env, R, C)
+        with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+            if op in ("+", "-"):
+                return a + b
+            if op in ("%", "*"):
+                return a * b
+            return a / np.abs(at(n.args[1], env, R, C))
+    raise ValueError(f"{op} is not element-wise")
+
+
+def evaluate_mag(node, env) -> np.ndarray:
+    """Magnitude scale of a whole result (same shape as ``evaluate``): the
+    element-wise ``at_mag``; a sum (accu, sum along a dimension) sums the
+    magnitudes of its terms; max takes the largest magnitude of the slice;
+    norm is the 2-norm of the magnitudes."""
+    n = parse(node)
+    if n.op not in REDUCTIONS:
+        r, c = shape_of(n, env)
+        out = np.empty((r, c))
+        for c0, c1 in _panels(r, c):
+            out[:, c0:c1] = np.broadcast_to(
+                at_mag(n, env, np.arange(r)[:, None], np.arange(c0, c1)[None, :]), (r, c1 - c0))
+        return out
+    inner = n.args[0]
+    r, c = shape_of(inner, env)
+    if n.op in ("accu", "norm"):
+        state = None
+        for c0, c1 in _panels(r, c):
+            m = np.broadcast_to(at_mag(inner, env, np.arange(r)[:, None],
+                                       np.arange(c0, c1)[None, :]), (r, c1 - c0))
+            state = neumaier_axis(m * m if n.op == "norm" else m, axis=1, state=state)
+        tot = _combine(*state) if state is not None else 0.0
+        return np.array([[math.sqrt(tot) if n.op == "norm" else tot]])
+    d = int(n.args[1].value)
+    out = np.zeros((1, c)) if d == 0 else np.zeros((r, 1))
+    for c0, c1 in _panels(r, c):
+        m = np.broadcast_to(at_mag(inner, env, np.arange(r)[:, None], np.arange(c0, c1)[None, :]),
+                            (r, c1 - c0))
+        if d == 0:
+            out[0, c0:c1] = np.max(m, axis=0) if n.op == "max" else np.sum(m, axis=0)
+        elif n.op == "max":
+            out[:, 0] = np.maximum(out[:, 0], np.max(m, axis=1))
+        else:
+            out[:, 0] += np.sum(m, axis=1)
+    return out
+
+
 # ---------------------------------------------------------------- whole results
 
 def _panels(rows, cols, budget=1 << 23):

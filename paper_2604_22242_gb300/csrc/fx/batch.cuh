@@ -8,8 +8,8 @@
 // memory). A tree with an accu output writes one compensated partial per
 // warp of each tile; a second launch sums each matrix's partials in order
 // in FP64 (one warp per matrix). The list, the descriptors and both launches are
-// cached per item array; with use_graph the launches are captured once in a
-// CUDA graph and replayed.
+// cached per item array (kept as a copy and compared whole on the next call);
+// with use_graph the launches are captured once in a CUDA graph and replayed.
 #pragma once
 
 #include <algorithm>
@@ -354,7 +354,11 @@ __global__ void __launch_bounds__(256) k_batch_combine(const BatchMat* __restric
 }
 
 struct BatchCacheEntry {
-  uint64_t key = 0;
+  // the item array and scalars the descriptors were built from: a call
+  // reuses them (and the captured graph) only when both compare equal
+  std::vector<fx_batch_item> items_seen;
+  double scal_seen[FX_MAX_SCALARS] = {};
+  bool built = false;
   int64_t n = 0, nitems = 0;
   Workspace dev;  // descriptors, items, partials
   BatchMat* mats = nullptr;
@@ -372,15 +376,6 @@ struct fx::BatchCache {
 };
 
 namespace fx {
-
-inline uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
-  const unsigned char* p = static_cast<const unsigned char*>(data);
-  for (size_t i = 0; i < n; ++i) {
-    h ^= p[i];
-    h *= 1099511628211ull;
-  }
-  return h;
-}
 
 template <class LL, int V, int I = 0>
 bool batch_leaf_check(const fx_batch_item& it, int64_t R, int64_t C, bool& vec, int& bad) {
@@ -494,14 +489,16 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
     if (!x->batch) x->batch = new (std::nothrow) BatchCache;
     if (!x->batch) return fail(FX_E_NOMEM, "out of host memory");
     BatchCacheEntry& c = x->batch->cur;
-    uint64_t key = fnv1a(items, size_t(n) * sizeof(fx_batch_item));
-    key = fnv1a(x->scal, sizeof x->scal, key);
-    key = fnv1a(&n, sizeof n, key);
+    const bool same = c.built && c.mats && c.n == n &&
+                      memcmp(c.scal_seen, x->scal, sizeof c.scal_seen) == 0 &&
+                      (n == 0 || memcmp(c.items_seen.data(), items,
+                                        size_t(n) * sizeof(fx_batch_item)) == 0);
     const int zs = n_in;
     const bool has_z = kind != FX_KIND_FULL_REDUCE;
     const bool has_s = kind != FX_KIND_ELEMENTWISE;
     const int sslot = has_z ? n_in + 1 : n_in;
-    if (key != c.key || !c.mats) {
+    if (!same) {
+      c.built = false;
       // validate and build the descriptors and the work-list
       std::vector<int64_t> order(n);
       for (int64_t i = 0; i < n; ++i) order[i] = i;
@@ -587,7 +584,9 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
       if (!work.empty())
         FX_CUDA(cudaMemcpyAsync(c.items, work.data(), sizeof(BatchItem) * work.size(), cudaMemcpyHostToDevice, st));
       FX_CUDA(cudaStreamSynchronize(st));  // host vectors die at scope end
-      c.key = key;
+      c.items_seen.assign(items, items + n);
+      memcpy(c.scal_seen, x->scal, sizeof c.scal_seen);
+      c.built = true;
       c.n = n;
       c.nitems = int64_t(work.size());
     }

@@ -24,9 +24,12 @@ static_assert(kScratchBytes == FX_NOALLOC_SCRATCH, "keep fx.h in step");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of the array, looked up once per device. In host code
+// Device address of the array, looked up once per device (the set-up done
+// by the first call on that device, with the device current). In host code
 // g_noalloc_scratch is only a host-side stand-in for the symbol, never a
-// device address, so the kernel is always given the looked-up pointer.
+// device address, so the kernel is always given the looked-up pointer. The
+// cached address belongs to the device's current context: after
+// cudaDeviceReset the entry point is not to be used again in the process.
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
@@ -84,6 +87,11 @@ extern "C" fx_status fx_sqdiff_accu_f32_noalloc(const float* A, const float* B, 
   if (!s) return fail(FX_E_ARG, "null output");
   if (rows < 0 || cols < 0) return fail(FX_E_SHAPE, "negative shape");
   if (ld < (rows > 1 ? rows : 1)) return fail(FX_E_ARG, "ld %lld < rows %lld", (long long)ld, (long long)rows);
+  // extents whose products overflow 64-bit indices are refused before any
+  // arithmetic on them
+  if (cols > 0 && (rows > INT64_MAX / cols || ld > (INT64_MAX - rows) / cols))
+    return fail(FX_E_SHAPE, "%lld x %lld (ld %lld) overflows 64-bit element indices",
+                (long long)rows, (long long)cols, (long long)ld);
   if (rows * cols > 0 && (!A || !B)) return fail(FX_E_ARG, "null input for a non-empty matrix");
   if (!aligned(A, 4) || !aligned(B, 4) || !aligned(s, 4))
     return fail(FX_E_ALIGN, "pointers must be aligned to 4 bytes");

@@ -135,15 +135,26 @@ def operands(seed: int, specs, storage: str, dist: str, lds: dict | None = None)
     """Matrices for named operands, one child stream each, in ``specs`` order.
 
     ``specs`` is a list of ``(name, rows, cols)``; ``lds`` optionally maps a
-    name to a leading dimension larger than its row count.
+    name to a leading dimension larger than its row count. Large operands
+    are drawn on a thread pool, one operand per thread: every operand has
+    its own stream, so the values do not depend on the threading.
     """
     lds = lds or {}
     kids = np.random.SeedSequence(seed).spawn(len(specs))
-    out = {}
-    for (name, r, c), ss in zip(specs, kids):
-        out[name] = matrix(np.random.Generator(np.random.PCG64(ss)), r, c, dist, storage,
-                           ld=lds.get(name))
-    return out
+
+    def one(job):
+        (name, r, c), ss = job
+        return name, matrix(np.random.Generator(np.random.PCG64(ss)), r, c, dist, storage,
+                            ld=lds.get(name))
+
+    jobs = list(zip(specs, kids))
+    big = sum(r * c for _, r, c in specs) >= (1 << 22) and len(specs) > 1
+    if big:
+        import concurrent.futures as cf
+        import os
+        with cf.ThreadPoolExecutor(min(len(jobs), os.cpu_count() or 1)) as ex:
+            return dict(ex.map(one, jobs))
+    return dict(one(j) for j in jobs)
 
 
 def batch_shapes(seed: int, count: int, lo: int = 16, hi: int = 2048):
@@ -170,12 +181,19 @@ def batch_operands(seed: int, count: int, layout, storage: str = "f32", dist: st
     """
     rows, cols = batch_shapes(seed, count, lo, hi)
     kids = np.random.SeedSequence(seed).spawn(len(layout) + 1)[1:]
-    out = {}
-    for (name, tr), ss in zip(layout, kids):
+
+    def one(job):
+        (name, tr), ss = job
         rng = np.random.Generator(np.random.PCG64(ss))
         mats = []
         for r, c in zip(rows.tolist(), cols.tolist()):
             rr, cc = (c, r) if tr else (r, c)
             mats.append(matrix(rng, rr, cc, dist, storage))
-        out[name] = mats
+        return name, mats
+
+    # one operand per thread (each has its own stream: same values either way)
+    import concurrent.futures as cf
+    import os
+    with cf.ThreadPoolExecutor(max(1, min(len(layout), os.cpu_count() or 1))) as ex:
+        out = dict(ex.map(one, list(zip(layout, kids))))
     return rows, cols, out

@@ -21,3 +21,22 @@ def fxlib():
     fxbuild.build()
     fx.lib()
     return fx
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Errors of the full-size comparisons against the oracle, one line each."""
+    try:
+        import harness
+    except ImportError:
+        return
+    if not harness.REPORTS:
+        return
+    tr = terminalreporter
+    tr.section("errors against the FP64 oracle (full-size outputs, every element)")
+    for label, d in harness.REPORTS:
+        def f(x):
+            return "-" if x is None else f"{x:.2e}"
+        tr.write_line(f"{label}: gate {d['gate']} err_sigma {f(d['max_scaled_err_sigma'])} "
+                      f"err_m {f(d['max_scaled_err_m'])} rel {d['max_plain_rel_err']:.2e} "
+                      f"tol {d['tol']:.0e} overflow {d['overflow_expected']} "
+                      f"nonfinite {d['nonfinite']} n {d['compared']}")

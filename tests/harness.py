@@ -1,12 +1,16 @@
 """Test harness: runs a compiled tree through the C ABI on synth inputs and
-compares it with the FP64 oracle using the scaled error metric.
+compares it with the FP64 oracle using the scaled error metric of
+``oracle.compare``:
 
-err_i = |gpu_i - oracle_i| / max(sigma_i, |oracle_i|, tiny)
+err_i = |gpu_i - oracle_i| / max(scale_i, |oracle_i|, tiny)
 
-where sigma is the oracle's running error bound (oracle.at_sigma). Outputs
-whose oracle value overflows the storage type must come out as an infinity
-of the same sign and are left out of the maximum; for FP16 outputs below
-the smallest normal the check is absolute (2^-24).
+where the scale is the oracle's magnitude scale m (oracle.at_mag) for trees
+of sums, products and scalars, and its running error bound sigma
+(oracle.at_sigma) for trees with transcendentals, divisions or matrix
+products (oracle.compare.gate_scale). Outputs whose oracle value overflows
+the storage type must come out as an infinity of the same sign and are left
+out of the maximum; for FP16 outputs below the smallest normal the check is
+absolute (2^-24).
 """
 from __future__ import annotations
 
@@ -14,11 +18,10 @@ import numpy as np
 
 import oracle
 import synth
+from oracle.compare import MAXFIN, TINY, ErrorReport, gate_scale, scaled_error  # noqa: F401
+from oracle.compare import tolerance as tolerance_of
 
 STORAGE_CODE = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
-MAXFIN = {"f32": float(np.finfo(np.float32).max), "f64": float(np.finfo(np.float64).max),
-          "bf16": float.fromhex("0x1.fep127"), "f16": 65504.0}
-TINY = {"f32": 2.0**-126, "f64": 2.0**-1022, "bf16": 2.0**-126, "f16": 2.0**-14}
 
 # Oracle trees for the compiled expressions (written from the paper's
 # notation, independently of the library's own formula strings).
@@ -72,15 +75,6 @@ for _n in range(2, 17):
 TRANSPOSED = {"schur_exp_trans": {"D"}, "schur_trans_accu": {"C"}, "expr2": {"B", "C"}}
 VECTORS = {"sigmoid_sqloss": {"b"}}
 
-TOL_EW = {"f64": 1e-13, "f32": 2e-6, "bf16": 8e-3, "f16": 1e-3}
-TOL_TRANS = {"f64": 1e-13, "f32": 1e-5, "bf16": 8e-3, "f16": 1e-3}
-# reductions of every storage type come out in FP32 (FP64 for f64) from a
-# compensated FP32 accumulation, so they are held to the FP32 reduction bound
-TOL_RED = {"f64": 1e-13, "f32": 1e-5, "bf16": 1e-5, "f16": 1e-5}
-HAS_TRANSCENDENTAL = {"schur_exp_trans", "schur_sqrt_sigmoid", "sigmoid_sqloss", "expr2",
-                      "sigmoid", "swish", "gelu", "gemm_epilogue", "expr3"}
-
-
 def tree_of(name, scalars=None):
     s = scalars if scalars is not None else DEFAULT_SCALARS.get(name, [])
     return TREES[name].format(**{f"s{i}": repr(float(v)) for i, v in enumerate(s)})
@@ -99,11 +93,8 @@ def specs_for(name, R, C):
 
 
 def tolerance(name, storage, output="Z"):
-    if output != "Z" or name in ("sqdiff_accu", "schur_colsum", "diff_norm", "sigmoid_sqloss"):
-        return TOL_RED[storage]
-    if name in HAS_TRANSCENDENTAL:
-        return TOL_TRANS[storage]
-    return TOL_EW[storage]
+    """The bound of output `output` ("Z", or "s"/"v" for a reduced output)."""
+    return tolerance_of(tree_of(name), storage, reduction=output != "Z")
 
 
 # ---------------------------------------------------------------- device side
@@ -229,56 +220,106 @@ def run(fx, name, storage, env, R, C, ldz=None, offset=0, unfused=False, scalars
 
 # ---------------------------------------------------------------- comparison
 
-def scaled_error(gpu, ref, sigma, storage):
-    """(max scaled error, #expected overflows, #bad non-finite, max plain rel)."""
-    gpu = np.asarray(gpu, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
-    sigma = np.broadcast_to(np.asarray(sigma, dtype=np.float64), ref.shape)
-    over = np.abs(ref) > MAXFIN[storage]
-    bad = 0
-    if np.any(over):
-        okinf = np.isinf(gpu[over]) & (np.sign(gpu[over]) == np.sign(ref[over]))
-        # a finite result is acceptable only when it is the largest finite value (rounding edge)
-        okmax = np.abs(gpu[over]) == MAXFIN[storage]
-        bad += int(np.sum(~(okinf | okmax)))
-    fin = ~over
-    g, r, s = gpu[fin], ref[fin], sigma[fin]
-    bad += int(np.sum(~np.isfinite(g)))
-    g = np.where(np.isfinite(g), g, np.inf)
-    denom = np.maximum(np.maximum(s, np.abs(r)), TINY[storage])
-    err = np.abs(g - r) / denom
-    if storage == "f16":
-        # Outputs below the FP16 normal range pass within one subnormal step
-        # (2^-24) of the oracle; beyond that only when cancellation explains
-        # the gap, i.e. it is within tolerance of the running error bound.
-        sub = np.abs(r) < 2.0**-14
-        d = np.abs(g[sub] - r[sub])
-        with np.errstate(divide="ignore", invalid="ignore"):
-            esub = np.where(d <= 2.0**-24, 0.0, d / np.maximum(s[sub], np.abs(r[sub])))
-        err[sub] = np.nan_to_num(esub, nan=np.inf)
-    nz = np.abs(r) > TINY[storage]
-    rel = float(np.max(np.abs(g[nz] - r[nz]) / np.abs(r[nz]))) if np.any(nz) else 0.0
-    return (float(np.max(err)) if err.size else 0.0), int(np.sum(over)), bad, rel
+def gate_of(name, scalars=None):
+    """"m" or "sigma": the scale the tree's results are held to."""
+    return gate_scale(tree_of(name, scalars))
 
 
-def oracle_outputs(name, env, scalars=None, sample=None):
-    """Oracle values and sigma: full matrices, or at `sample` = (R, C) index arrays."""
+def _pick(v, sg, mg, scale, gate):
+    if scale == "both":
+        return (v, sg, mg)
+    if scale == "sigma" or (scale == "gate" and gate == "sigma"):
+        return (v, sg)
+    return (v, mg)
+
+
+def oracle_outputs(name, env, scalars=None, sample=None, scale="gate"):
+    """Oracle values and their scale: full matrices, or at `sample` = (R, C)
+    index arrays. scale: "gate" (the tree's gating scale), "sigma", "m", or
+    "both" (triples value, sigma, m)."""
     tree = tree_of(name, scalars)
-    if name == "schur_trans_accu":
+    gate = gate_scale(tree)
+    need_s = scale in ("both", "sigma") or (scale == "gate" and gate == "sigma")
+    need_m = scale in ("both", "m") or (scale == "gate" and gate == "m")
+
+    def elementwise(t):
         if sample is None:
-            z, sz = oracle.evaluate_sigma(tree, env)
-            res = {"Z": (z, sz)}
+            v, sg = oracle.evaluate_sigma(t, env) if need_s else (oracle.evaluate(t, env), None)
+            mg = oracle.evaluate_mag(t, env) if need_m else None
         else:
-            res = {"Z": oracle.at_sigma(tree, env, *sample)}
-        s, ss = oracle.evaluate_sigma(f"(accu {tree})", env)
-        res["s"] = (s[0, 0], ss[0, 0])
+            v, sg = oracle.at_sigma(t, env, *sample) if need_s else (oracle.at(t, env, *sample), None)
+            mg = oracle.at_mag(t, env, *sample) if need_m else None
+        return v, sg, mg
+
+    def reduction(t):
+        v, sg = oracle.evaluate_sigma(t, env) if need_s else (oracle.evaluate(t, env), None)
+        mg = oracle.evaluate_mag(t, env) if need_m else None
+        return v, sg, mg
+
+    if name == "schur_trans_accu":
+        res = {"Z": _pick(*elementwise(tree), scale, gate)}
+        v, sg, mg = reduction(f"(accu {tree})")
+        res["s"] = _pick(v[0, 0], None if sg is None else sg[0, 0],
+                         None if mg is None else mg[0, 0], scale, gate)
         return res
     root = oracle.parse(tree)
     if root.op in oracle.REDUCTIONS:
-        v, sv = oracle.evaluate_sigma(tree, env)
+        v, sg, mg = reduction(tree)
         if root.op in ("accu", "norm"):
-            return {"s": (v[0, 0], sv[0, 0])}
-        return {"v": (v.ravel(), sv.ravel())}
-    if sample is None:
-        return {"Z": oracle.evaluate_sigma(tree, env)}
-    return {"Z": oracle.at_sigma(tree, env, *sample)}
+            return {"s": _pick(v[0, 0], None if sg is None else sg[0, 0],
+                               None if mg is None else mg[0, 0], scale, gate)}
+        return {"v": _pick(v.ravel(), None if sg is None else sg.ravel(),
+                           None if mg is None else mg.ravel(), scale, gate)}
+    return {"Z": _pick(*elementwise(tree), scale, gate)}
+
+
+# ---------------------------------------------------------------- full-size comparison
+
+# (label, ErrorReport.as_dict()) of the full-size comparisons of this session,
+# printed at the end of the pytest run (conftest.pytest_terminal_summary)
+REPORTS = []
+
+
+def record(label, rep):
+    REPORTS.append((label, rep.as_dict()))
+
+def _workers():
+    import os
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def panel_report(name, storage, Z, env, scalars=None, both=False, budget=1 << 22):
+    """Element-by-element comparison of a whole element-wise output Z (an
+    R x C FP64 array) with the oracle, column panel by column panel on a
+    thread pool (numpy releases the interpreter lock in its array loops).
+    Returns an ErrorReport under the tree's gate scale (and, with `both`,
+    the other scale as well)."""
+    from concurrent.futures import ThreadPoolExecutor
+    tree = tree_of(name, scalars)
+    gate = gate_scale(tree)
+    R, C = Z.shape
+    w = max(1, budget // max(R, 1))
+    panels = [(c0, min(C, c0 + w)) for c0 in range(0, C, w)]
+    want_s = both or gate == "sigma"
+    want_m = both or gate == "m"
+
+    def one(p):
+        c0, c1 = p
+        rr, cc = np.arange(R)[:, None], np.arange(c0, c1)[None, :]
+        if want_s:
+            v, sg = oracle.at_sigma(tree, env, rr, cc)
+        else:
+            v, sg = oracle.at(tree, env, rr, cc), None
+        mg = oracle.at_mag(tree, env, rr, cc) if want_m else None
+        rep = ErrorReport(storage, tolerance(name, storage), gate)
+        shape = (R, c1 - c0)
+        rep.add(Z[:, c0:c1], np.broadcast_to(v, shape),
+                None if sg is None else np.broadcast_to(sg, shape),
+                None if mg is None else np.broadcast_to(mg, shape))
+        return rep
+
+    total = ErrorReport(storage, tolerance(name, storage), gate)
+    with ThreadPoolExecutor(_workers()) as ex:
+        for rep in ex.map(one, panels):
+            total.merge(rep)
+    return total

@@ -110,15 +110,50 @@ def test_backward_repeatable(fx):
         assert np.array_equal(a[s], b[s]), s
 
 
+def gradient_reports(got, env, storage, block=128):
+    """Every element of every gradient against the oracle's reverse pass:
+    the output rows in blocks of `block` (a row block of X, W, Y is read only
+    by those output rows, and b(i) only by row i, so each block's gradient
+    entries are exact), evaluated on a thread pool."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from harness import _workers
+    from oracle.compare import ErrorReport
+    R = env["X"].rows
+
+    def one(r0):
+        ref = ograd.gradient_sigma(LOSS, env, 1.0, rows=np.arange(r0, min(R, r0 + block)))
+        out = {}
+        for s_, (idx, v, sg) in ref.items():
+            if s_ in got:
+                out[s_] = ErrorReport(storage, TOL[storage], "sigma").add(got[s_][idx], v, sg)
+        return out
+
+    total = {}
+    with ThreadPoolExecutor(_workers()) as ex:
+        for part in ex.map(one, range(0, R, block)):
+            for s_, rep in part.items():
+                if s_ in total:
+                    total[s_].merge(rep)
+                else:
+                    total[s_] = rep
+    return total
+
+
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
-def test_gradients_8192_sampled_rows_and_finite_differences(fx, storage):
+def test_gradients_8192_all_elements_and_finite_differences(fx, storage):
+    from harness import record
     R = C = 8192
     env = env_for(storage, R, C)
     got, _ = gpu_grads(fx, storage, env)
+    reps = gradient_reports(got, env, storage)
+    for s_, rep in reps.items():
+        record(f"sigmoid_sqloss/{storage}/d{s_} at 8192^2", rep)
+        assert rep.nonfinite == 0, f"d{s_}: non-finite"
+        assert rep.err <= TOL[storage], f"d{s_} at 8192^2: scaled error {rep.err:.3e}"
+        assert rep.n == (R if s_ == "b" else R * C)
     rng = np.random.default_rng(3)
     rows = np.sort(rng.choice(R, 64, replace=False))
-    ref = ograd.gradient_sigma(LOSS, env, 1.0, rows=rows)
-    check_grads(got, ref, storage, "at 8192^2 (sampled rows)")
     # finite differences: L is a sum of per-element terms, so perturbing X(i,j)
     # or W(i,j) changes term (i,j) only, and b(i) changes row i only
     f64 = {s: env[s].f64() for s in SLOTS}

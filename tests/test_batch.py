@@ -3,13 +3,9 @@ many matrices of uneven shapes in one persistent launch (GPU)."""
 import numpy as np
 import pytest
 
-import oracle
 import synth
-from harness import from_device, scaled_error
 
 pytestmark = pytest.mark.gpu
-
-TREE = "(+ (% A B) (* 0.5 (t C)))"
 
 
 @pytest.fixture(scope="module")
@@ -79,15 +75,34 @@ def run_batch(fx, rows, cols, ops, use_graph, repeat=1, storage=0, shape=None, t
     return zs, S.cpu().numpy().astype(np.float64), launches
 
 
-def check(ops, rows, cols, zs, ss, which):
-    for i in which:
+def check(ops, rows, cols, zs, ss, which, report=None):
+    """Every listed matrix's Z and s against the oracle (gate scale of the
+    tree), on a thread pool; with `report` = (label, ...) the summary is
+    recorded for the end-of-run error table."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from harness import _workers, oracle_outputs, record
+    from oracle.compare import ErrorReport
+
+    def one(i):
         env = {k: ops[k][i] for k in "ABC"}
-        z, sz = oracle.evaluate_sigma(TREE, env)
-        err, _, bad, _ = scaled_error(zs[i], z, sz, "f32")
-        assert bad == 0 and err <= 2e-6, (i, rows[i], cols[i], err)
-        v, sv = oracle.evaluate_sigma(f"(accu {TREE})", env)
-        err, _, bad, _ = scaled_error([ss[i]], [v[0, 0]], [sv[0, 0]], "f32")
-        assert bad == 0 and err <= 1e-5, (i, "s", err)
+        ref = oracle_outputs("schur_trans_accu", env)
+        z, sz = ref["Z"]
+        rz = ErrorReport("f32", 2e-6, "m").add(zs[i], z, mag=sz)
+        v, sv = ref["s"]
+        rs = ErrorReport("f32", 1e-5, "m").add([ss[i]], [v], mag=[sv])
+        assert rz.nonfinite == 0 and rz.err <= 2e-6, (i, rows[i], cols[i], rz.err)
+        assert rs.nonfinite == 0 and rs.err <= 1e-5, (i, "s", rs.err)
+        return rz, rs
+
+    tz, ts = ErrorReport("f32", 2e-6, "m"), ErrorReport("f32", 1e-5, "m")
+    with ThreadPoolExecutor(_workers()) as ex:
+        for rz, rs in ex.map(one, list(which)):
+            tz.merge(rz)
+            ts.merge(rs)
+    if report:
+        record(f"{report} Z", tz)
+        record(f"{report} s", ts)
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
@@ -110,12 +125,14 @@ def test_graph_replay_matches_direct(fx):
 
 
 def test_batch_4096_log_uniform(fx):
+    """The batch the benchmark times: 4096 matrices, rows and cols
+    log-uniform in [16, 2048] (seed 2), the launch shape autotuned as the
+    benchmark does, graph-replayed; every element of every matrix compared."""
     rows, cols, ops = synth.batch_operands(2, 4096, [("A", False), ("B", False), ("C", True)])
-    zs, ss, _ = run_batch(fx, rows, cols, ops, True, repeat=2)
-    rng = np.random.default_rng(2)
-    which = sorted(set(rng.choice(4096, 48, replace=False).tolist()) |
-                   {int(np.argmax(rows * cols)), int(np.argmin(rows * cols))})
-    check(ops, rows, cols, zs, ss, which)
+    shape = []
+    zs, ss, _ = run_batch(fx, rows, cols, ops, True, repeat=2, tune="search", shape_out=shape)
+    check(ops, rows, cols, zs, ss, range(len(rows)),
+          report=f"schur_trans_accu/f32 batch of 4096 (shape {shape[0]})")
     assert np.all(np.isfinite(ss))
 
 

@@ -83,3 +83,33 @@ def test_recorded_traffic_matches_source_and_shape():
     alg_read, alg_write = 4 * 8192 * 8192 * 4, 8192 * 8192 * 4
     for b in tr["bytes"].values():
         assert alg_read <= b <= alg_read * 1.001 + alg_write
+
+
+def test_oracle_check_leg_on_cpu_tensors():
+    """bench.oracle_errors on outputs held in CPU tensors: the oracle's own
+    values rounded to the storage type pass, and a planted error fails."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import synth
+    R, C = 64, 48
+    env = synth.operands(1, [("X", R, C), ("Y", R, C), ("W", R, C), ("V", R, C)], "f32", "normal")
+    keep = {"env": env, "trees": []}
+    for name, key, ins, kind in [("schur_sqrt_sigmoid", "Z", "XYWV", "Z"),
+                                 ("schur_colsum", "colsum", "XY", "col"),
+                                 ("absdiff_rowmax", "rowmax", "XY", "row"),
+                                 ("diff_norm", "nrm", "XY", "s")]:
+        v = oracle.evaluate(bench.ORACLE_OF[name], env)
+        flat = v.T.ravel() if kind == "Z" else v.ravel()
+        keep[key] = (None, torch.from_numpy(flat.astype(np.float32)))
+        keep["trees"].append((name, key, list(ins), kind))
+    errs = bench.oracle_errors(keep, "f32", n_sample=512)
+    assert set(errs) == {"Z", "colsum", "rowmax", "nrm"}
+    for k, d in errs.items():
+        assert d["ok"], (k, d)
+        assert d["gate"] == ("sigma" if k == "Z" else "m")
+        assert d["max_scaled_err_sigma"] is not None and d["max_scaled_err_m"] is not None
+    keep["colsum"][1][3] += 0.01 * float(keep["colsum"][1].abs().max())
+    assert not bench.oracle_errors(keep, "f32", n_sample=512)["colsum"]["ok"]

@@ -328,7 +328,7 @@ def _f32_eval(node, env, R, C):
                 "tanh": lambda: np.tanh(a)}[op]().astype(f)
     b = _f32_eval(n.args[1], env, R, C)
     return {"+": lambda: a + b, "-": lambda: a - b, "%": lambda: a * b, "*": lambda: a * b,
-            "/": lambda: a / b}[op]().astype(f)
+            "/": lambda: a / b, "gt": lambda: a > b}[op]().astype(f)
 
 
 TREES = [
@@ -438,6 +438,88 @@ def test_sigma_reduction_rules():
     assert s[0, 0] == pytest.approx(2 * prod.sum(), rel=1e-12)
     v, s = oracle.evaluate_sigma("(max (abs (- A B)) 1)", env)
     assert np.allclose(s, v, rtol=1e-15)
+
+
+# ------------------------------------------------------------ magnitude scale m
+
+def test_magnitude_scale_by_hand():
+    """m evaluates the tree on magnitudes: |a|+|b| for a sum or difference,
+    |a||b| for a Schur product, |s||a| for a scalar, square of the
+    magnitude; worked on a 2 x 2 case with mixed signs."""
+    X = buf([1.0, -2.0, 3.0, -4.0], 2, 2)
+    Y = buf([-0.5, 0.25, 2.0, -8.0], 2, 2)
+    env = {"X": X, "Y": Y}
+    R, C = np.arange(2)[:, None], np.arange(2)[None, :]
+    ax = np.array([[1.0, 3.0], [2.0, 4.0]])
+    ay = np.array([[0.5, 2.0], [0.25, 8.0]])
+    assert np.array_equal(oracle.at_mag("(- X Y)", env, R, C), ax + ay)
+    assert np.array_equal(oracle.at_mag("(+ X Y)", env, R, C), ax + ay)
+    assert np.array_equal(oracle.at_mag("(% X Y)", env, R, C), ax * ay)
+    assert np.array_equal(oracle.at_mag("(* -3 X)", env, R, C), 3 * ax)
+    assert np.array_equal(oracle.at_mag("(square (- X Y))", env, R, C), (ax + ay) ** 2)
+    assert np.array_equal(oracle.at_mag("(abs (neg X))", env, R, C), ax)
+    # X - X is exactly 0, but its scale is 2|X|: a cancellation is visible in m
+    assert np.all(oracle.evaluate("(- X X)", env) == 0)
+    assert np.array_equal(oracle.at_mag("(- X X)", env, R, C), 2 * ax)
+    # the transposed leaf maps positions the same way as the value rule
+    assert np.array_equal(oracle.at_mag("(+ (t X) Y)", env, R, C), ax.T + ay)
+    # the mask is exact: its scale is its value
+    assert np.array_equal(oracle.at_mag("(% X (gt X 0))", env, R, C), ax * (np.array(
+        [[1.0, 1.0], [0.0, 0.0]])))
+
+
+def test_magnitude_scale_reductions_closed_forms():
+    env = synth.operands(24, [("X", 37, 23), ("Y", 37, 23)], "f64", "normal")
+    x, y = (np.abs(env[k].f64().reshape(23, 37).T) for k in "XY")
+    m = x + y
+    assert oracle.evaluate_mag("(accu (- X Y))", env)[0, 0] == pytest.approx(
+        math.fsum(m.ravel()), rel=1e-15)
+    assert oracle.evaluate_mag("(norm (- X Y))", env)[0, 0] == pytest.approx(
+        math.sqrt(math.fsum((m * m).ravel())), rel=1e-15)
+    assert np.allclose(oracle.evaluate_mag("(sum (% X Y) 0)", env)[0], (x * y).sum(axis=0),
+                       rtol=1e-14, atol=0)
+    assert np.allclose(oracle.evaluate_mag("(sum (% X Y) 1)", env)[:, 0], (x * y).sum(axis=1),
+                       rtol=1e-14, atol=0)
+    assert np.array_equal(oracle.evaluate_mag("(max (abs (- X Y)) 1)", env)[:, 0],
+                          m.max(axis=1))
+    assert np.array_equal(oracle.evaluate_mag("(max (abs (- X Y)) 0)", env)[0], m.max(axis=0))
+
+
+M_TREES = ["(+ (+ (+ A B) C) (t D))", "(- (+ A C) (+ B C))", "(+ (% A B) (* 0.5 (t D)))",
+           "(% (+ A B) (- C (t D)))", "(% A (gt A 0))", "(- (square (- A B)) (abs C))"]
+
+
+@pytest.mark.parametrize("tree", M_TREES)
+def test_magnitude_scale_bounds_float32_rounding(tree):
+    """For trees of sums, products and scalars, a step-by-step FP32
+    evaluation errs by a few u m; the scale never falls below |value|."""
+    r = c = 48
+    env = synth.operands(25, [("A", r, c), ("B", r, c), ("C", r, c), ("D", c, r)], "f32",
+                         "normal")
+    # C large against A and B: (A + C) - (B + C) cancels to about A - B
+    env["C"].data[:] = (env["C"].data * 1000).astype(np.float32)
+    R, C = np.arange(r)[:, None], np.arange(c)[None, :]
+    z = oracle.at(tree, env, R, C)
+    m = oracle.at_mag(tree, env, R, C)
+    z32 = _f32_eval(tree, env, R, C).astype(np.float64)
+    u = 2.0 ** -24
+    assert np.all(m >= np.abs(z))
+    assert np.all(np.abs(z32 - z) <= 4 * u * m + 1e-300)
+    if tree == "(- (+ A C) (+ B C))":
+        # a scale of |value| alone (no magnitude of the cancelled terms)
+        # would not bound that evaluation
+        assert np.any(np.abs(z32 - z) > 4 * u * np.abs(z))
+
+
+def test_gate_scale_rule():
+    from oracle.compare import gate_scale
+    for t in ("(+ A B)", "(accu (square (- A B)))", "(sum (% X Y) 0)", "(max (abs (- X Y)) 1)",
+              "(norm (- X Y))", "(% X (gt X 0))", "(+ (* 2 (+ (t X) Y)) (* 2 (+ X (t Y))))"):
+        assert gate_scale(t) == "m", t
+    for t in ("(- (+ (% A B) (* 3.5 (exp C))) (t D))", "(/ X (+ 1 (exp (neg X))))",
+              "(sigmoid (+ (* 0.5 (* X Y)) W))", "(* 2 (* X (t Y)))", "(log (pow D 2))",
+              "(/ A B)"):
+        assert gate_scale(t) == "sigma", t
 
 
 # ------------------------------------------------------------ gradient

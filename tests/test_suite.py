@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from harness import oracle_outputs, run, scaled_error, specs_for, tolerance
+from harness import oracle_outputs, panel_report, record, run, scaled_error, specs_for, tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -126,3 +126,36 @@ def test_unfused_suite(fx):
         env = synth.operands(62, specs_for(name, R, C), "f32", "normal")
         got = run(fx, name, "f32", env, R, C, unfused=True)
         check(name, got, env, " (unfused)")
+
+
+# ---------------------------------------------------------------- Sec. 4 sizes
+
+@pytest.fixture(scope="module")
+def suite10k():
+    """The benchmark's 10000^2 FP32 inputs: A1..A16 U[-1, 1] (seed 4); P1, P2
+    U[0.5, 2] (seed 5) and Y64 FP64 N(0, 1) (seed 6) for expr3."""
+    R = C = 10000
+    env = synth.operands(4, [(f"A{k}", R, C) for k in range(1, 17)], "f32", "uniform")
+    env.update(synth.operands(5, [("P1", R, C), ("P2", R, C)], "f32", "positive"))
+    env.update(synth.operands(6, [("Y64", R, C)], "f64", "normal"))
+    return env
+
+
+# the benchmark's binding of those inputs to each tree's slots
+BENCH_INPUTS = {"add16": [f"A{k}" for k in range(1, 17)], "expr1": ["A1", "A2"],
+                "expr2": ["A1", "A2", "A3", "A4"], "expr3": ["P1", "Y64", "P2"], "gelu": ["A1"]}
+
+
+@pytest.mark.parametrize("name", ["add16", "expr1", "expr2", "expr3", "gelu"])
+def test_suite_10000_autotuned(fx, suite10k, name):
+    """The Sec. 4 expressions at the paper's 10000^2 size, autotuned as the
+    benchmark runs them, every output element against the oracle."""
+    from harness import SLOTS
+    R = C = 10000
+    env = {slot: suite10k[src] for slot, src in zip(SLOTS[name], BENCH_INPUTS[name])}
+    got = run(fx, name, "f32", env, R, C, tune="search")
+    rep = panel_report(name, "f32", got["Z"], env)
+    record(f"{name}/f32/Z at 10000^2 (shape {got['_shape']})", rep)
+    assert rep.nonfinite == 0
+    assert rep.err <= rep.tol, f"{name} at 10000^2: scaled error {rep.err:.3e} > {rep.tol:.1e}"
+    assert rep.n == R * C

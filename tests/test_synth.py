@@ -70,3 +70,15 @@ def test_batch_operands_transposed_layout():
     for i in range(5):
         assert (ops["A"][i].rows, ops["A"][i].cols) == (rows[i], cols[i])
         assert (ops["C"][i].rows, ops["C"][i].cols) == (cols[i], rows[i])
+
+
+def test_threaded_draws_match_one_stream_per_operand():
+    """Large operand sets are drawn on threads; each operand still comes from
+    its own child stream, so the values equal a one-by-one draw."""
+    specs = [("A", 1024, 1100), ("B", 1024, 1100), ("C", 1100, 1024)]
+    got = synth.operands(9, specs, "bf16", "lognormal_signed")
+    kids = np.random.SeedSequence(9).spawn(3)
+    for (name, r, c), ss in zip(specs, kids):
+        want = synth.matrix(np.random.Generator(np.random.PCG64(ss)), r, c, "lognormal_signed",
+                            "bf16")
+        assert np.array_equal(got[name].data, want.data), name
