@@ -171,8 +171,10 @@ def _bind(fx, h, k, t, rows, cols, ld):
     fx.fx_expr_bind(h, k, t.data_ptr(), rows, cols, ld)
 
 
-def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
-    """Ops for single-matrix trees. trees: [(name, key, input names, out kind)]."""
+def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep, check=True):
+    """Ops for single-matrix trees. trees: [(name, key, input names, out kind)];
+    out kind "Zs" is a matrix Z plus a scalar s from one launch. With check,
+    the outputs are compared with the oracle after the timed region."""
     import numpy as np
     code = {"f32": fx.FX_F32, "f64": fx.FX_F64, "bf16": fx.FX_BF16, "f16": fx.FX_F16}[storage]
     tdt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16,
@@ -180,14 +182,16 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
     rdt = torch.float64 if storage == "f64" else torch.float32
     es = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[storage]
     rs = 8 if storage == "f64" else 4
-    d = {}
-    for k, b in env.items():
-        if storage == "bf16":
-            t = torch.from_numpy(b.data.view(np.int16)).view(torch.bfloat16)
-        else:
-            t = torch.from_numpy(b.data)
-        d[k] = t.to(dev)
-    keep["inputs"] = d
+    d = keep.get("inputs")
+    if d is None:
+        d = {}
+        for k, b in env.items():
+            if storage == "bf16":
+                t = torch.from_numpy(b.data.view(np.int16)).view(torch.bfloat16)
+            else:
+                t = torch.from_numpy(b.data)
+            d[k] = t.to(dev)
+        keep["inputs"] = d
     ops = []
     for name, key, ins, kind in trees:
         h = fx.fx_expr_create(name, code)
@@ -205,6 +209,11 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
             o = torch.empty(1, dtype=rdt, device=dev)
             _bind(fx, h, len(ins), o, 1, 1, 1)
             nb += rs
+        elif kind == "Zs":
+            o = (torch.empty(R * C, dtype=tdt, device=dev), torch.empty(1, dtype=rdt, device=dev))
+            _bind(fx, h, len(ins), o[0], R, C, R)
+            _bind(fx, h, len(ins) + 1, o[1], 1, 1, 1)
+            nb += R * C * es + rs
         elif kind == "col":
             o = torch.empty(C, dtype=rdt, device=dev)
             _bind(fx, h, len(ins), o, 1, C, 1)
@@ -215,7 +224,8 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep):
             nb += R * rs
         keep[key] = (h, o)
         keep.setdefault("_handles", []).append(h)
-        keep.setdefault("trees", []).append((name, key, list(ins), kind))
+        if check:
+            keep.setdefault("trees", []).append((name, key, list(ins), kind))
         ops.append(Op(key, nb, (lambda h=h: fx.fx_eval(h, sp)),
                       (lambda h=h: fx.fx_eval_unfused(h, sp)),
                       (lambda h=h: fx.fx_expr_last_launches(h))))
@@ -245,7 +255,10 @@ def workload(name, fx, torch, dev, sp, keep, size=8192, count=4096):
         dist = "uniform" if name == "small1024" else "lognormal_signed"
         env = synth.operands(0, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], storage, dist)
         inputs = f"A,B,C,D {dist}, seed 0, column-major"
-        trees = [("schur_exp_trans", "Z", "ABCD", "Z"), ("sqdiff_accu", "s", "AB", "s")]
+        # Z and s in one pass over A, B, C, D; the two separate trees are
+        # timed beside it ("separate_trees") for comparison
+        trees = [("schur_exp_trans_sqdiff", "Zs", "ABCD", "Zs")]
+        sep = [("schur_exp_trans", "Z_alone", "ABCD", "Z"), ("sqdiff_accu", "s_alone", "AB", "s")]
         if name.endswith("_clamped"):
             # C's values capped at 9: 3.5 exp(9) = 28361 stays finite in FP16
             c = env["C"]
@@ -253,14 +266,14 @@ def workload(name, fx, torch, dev, sp, keep, size=8192, count=4096):
             env["C"] = synth.Buffer(np.where(synth.to_f64(c.data, storage) > 9.0, cap, c.data),
                                     c.rows, c.cols, c.ld, storage)
             inputs += "; C capped at 9"
-            trees = trees[:1]
-        cfg = {"workload": f"A%B+3.5*exp(C)-trans(D) and accu(square(A-B)) at {R}x{C}",
+        cfg = {"workload": f"A%B+3.5*exp(C)-trans(D) and accu(square(A-B)) in one pass at {R}x{C}",
                "rows": R, "cols": C, "inputs": inputs,
                "l2": "L2 flushed before every kernel (256 MiB write), device-timed per kernel"
                if name == "small1024" else "inputs larger than L2, no flush"}
         keep["env"] = env
-        return (_expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep), cfg, "Z",
-                name == "small1024", storage)
+        ops = _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep)
+        keep["alt_ops"] = _expr_ops(fx, torch, dev, sp, sep, storage, env, R, C, keep, check=False)
+        return ops, cfg, "Zs", name == "small1024", storage
     if name == "batch4096":
         return batch_workload(fx, torch, dev, sp, keep, count)
     if name == "suite10k":
@@ -508,6 +521,7 @@ ORACLE_OF = {
     "diff_norm": "(norm (- X Y))",
     "schur_exp_trans": "(- (+ (% A B) (* 3.5 (exp C))) (t D))",
     "sqdiff_accu": "(accu (square (- A B)))",
+    "schur_exp_trans_sqdiff": ("(- (+ (% A B) (* 3.5 (exp C))) (t D))", "(accu (square (- A B)))"),
     "schur_trans_accu": "(+ (% A B) (* 0.5 (t C)))",
     "sigmoid_sqloss": "(accu (square (- (sigmoid (+ (% X W) (each_col b))) Y)))",
 }
@@ -535,6 +549,18 @@ def oracle_errors(keep, storage, n_sample=1 << 16):
     for name, key, ins, kind in keep.get("trees", []):
         tree = ORACLE_OF[name]
         _, o = keep[key]
+        if kind == "Zs":     # Z of the first tree, s = accu of the second
+            tree, side = tree
+            o, osum = o
+            g = _host64(osum).ravel()
+
+            def sjob(side=side, g=g):
+                v, sg = oracle.evaluate_sigma(side, env)
+                m = oracle.evaluate_mag(side, env)
+                return ErrorReport(rst, tolerance(side, storage), gate_scale(side)).add(
+                    g, v.ravel(), sg.ravel(), m.ravel())
+            jobs["s"] = sjob
+            key, kind = "Z", "Z"
         if kind == "Z":
             first = env[ins[0]]
             R, C = first.rows, first.cols
@@ -714,6 +740,14 @@ def unfused_steps(torch, stream, ops, K, fl):
     return {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in uev.items()}
 
 
+def refresh_outputs(torch, ops):
+    """The unfused baseline writes the same output buffers: run every fused
+    op once more, so that the oracle check reads what the fused path wrote."""
+    for o in ops:
+        o.launch()
+    torch.cuda.synchronize()
+
+
 def release(fx, torch, keep):
     """Frees a workload's expression objects and device buffers."""
     torch.cuda.synchronize()
@@ -745,6 +779,21 @@ def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
         with torch.cuda.stream(stream):
             per_all, ms, launches, _, _ = timed_steps(torch, stream, ops, K, W, fl)
             u_ms = unfused_steps(torch, stream, ops, K, fl)
+            alt = None
+            if keep.get("alt_ops"):
+                aops = keep["alt_ops"]
+                for h in [keep[o.key][0] for o in aops]:
+                    if not args.no_tune and not args.shape:
+                        fx.fx_tune(h, "search", sp)
+                a_all, a_ms, _, _, _ = timed_steps(torch, stream, aops, K, W, fl)
+                if flush:
+                    a_ms = K * sum(statistics.mean(v) for v in a_all.values())
+                a_bytes = sum(o.bytes for o in aops)
+                alt = {"what": "the same results from separate trees, one launch each",
+                       "ms_per_step": round(a_ms / K, 4), "bytes_per_step": a_bytes,
+                       "launches_per_step": len(aops),
+                       "gbs": round(a_bytes * K / (a_ms / 1e3) / 1e9, 2),
+                       "per_op_ms": {k: round(statistics.mean(v), 4) for k, v in a_all.items()}}
         per_ms = {k: statistics.mean(v) for k, v in per_all.items()}
         if flush:
             ms = K * sum(per_ms.values())
@@ -768,6 +817,9 @@ def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
             "gpu_launches": launches, "launch_shape": cfg.get("launch_shape"), "l2": cfg["l2"],
             "inputs": cfg.get("inputs"),
         }
+        refresh_outputs(torch, ops)
+        if alt:
+            out["separate_trees"] = alt
         if (name, dom) in FP64_PIPE_OPS:
             alu = fp64_roofline(fx, sp, name, dom, dom_op, per_ms[dom], peak, storage, cfg)
             if alu:
@@ -884,6 +936,8 @@ def run_ours(args, rank, world):
     if e2e:
         line["e2e"] = e2e
     if not args.no_check:
+        with torch.cuda.stream(stream):
+            refresh_outputs(torch, ops)
         line["errors"] = oracle_errors(keep, storage)
     if world == 1 and args.workload == "expr8192" and args.size == 8192 and not args.no_configs:
         release(fx, torch, keep)

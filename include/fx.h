@@ -62,7 +62,9 @@ typedef enum {
   FX_KIND_ELEMENTWISE = 0, /* one output matrix, same shape as the tree */
   FX_KIND_FULL_REDUCE = 1, /* accu / norm: one scalar */
   FX_KIND_DIM_REDUCE = 2,  /* sum / max along a dimension: a row or column vector */
-  FX_KIND_MULTI = 3        /* output matrix Z plus the scalar accu(Z) */
+  FX_KIND_MULTI = 3        /* output matrix Z plus one scalar s: accu(Z), or the
+                              accu of a second tree over the same leaves (the
+                              formula then lists both trees, "Z-tree ; s-tree") */
 } fx_kind;
 
 /* Autotuner modes (fx_tune). */

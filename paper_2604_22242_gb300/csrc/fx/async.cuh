@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(NT) k_tile_async(const E e, const Slots sl, co
           load_vtile<LL, V, CT, TR, TC>(p, buf, sl, r0, c0, r, c, nvalid);
           CT v[V];
           eval_lanes<V>(e, p, v);
-          epi.put(st, (r0 + r) + (c0 + c) * epi.ldz, v, nvalid);
+          epi_put(epi, st, (r0 + r) + (c0 + c) * epi.ldz, v, p, nvalid);
         }
       }
     }

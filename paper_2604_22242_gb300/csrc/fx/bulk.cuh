@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(NTC + 32) k_flat_bulk(const E e, const Slots s
           load_flat_chunk<LL, V, CT, CH>(p, stage, kk);
           CT v[V];
           eval_lanes<V>(e, p, v);
-          epi.put(st, i0 + kk, v, V);
+          epi_put(epi, st, i0 + kk, v, p, V);
         }
       }
       tma::arrive(&ring.empty[s]);
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(NTC + 32) k_flat_bulk(const E e, const Slots s
         CT v[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) v[j] = v1[0];
-        epi.put(st, i, v, 1);
+        epi_put(epi, st, i, v, q, 1);
       }
     }
   }
@@ -347,11 +347,11 @@ __global__ void __launch_bounds__(NTC + 32) k_row_bulk(const E e, const Slots sl
   const int64_t r = r0 + int64_t(t) * V;
   const int nvalid = clamp_valid(R - r, V);
   ThreadSum<CT> acc[V];
-  CT m[V];
+  max_acc_t<E, CT> mx[V];
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     acc[j].init();
-    m[j] = neg_inf<CT>();
+    mx[j].init();
   }
   Pack<LL, V, CT> hold;
   load_hold(hold, sl, r, nvalid);
@@ -374,13 +374,16 @@ __global__ void __launch_bounds__(NTC + 32) k_row_bulk(const E e, const Slots sl
         eval_lanes<V>(e, p, v);
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-          if (ISMAX) m[q] = max_nan(m[q], v[q]);
+          if (ISMAX) mx[q].add(v[q]);
           else acc[q].add(v[q]);
         }
       }
     }
     tma::arrive(&ring.empty[st]);
   }
+  CT m[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) m[j] = mx[j].get();
   row_finish<ISMAX, V, CT>(rr, acc, m, R, r, nvalid, s, NTC, &ring.abort);
 }
 

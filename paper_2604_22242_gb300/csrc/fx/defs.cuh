@@ -45,6 +45,20 @@ struct SqdiffAccu {
   }
 };
 
+// The 1024^2 workload's two results in one pass over A, B, C, D:
+// Z = A % B + 3.5 * exp(C) - trans(D) and s = accu(square(A - B))
+struct SchurExpTransSqdiff {
+  FX_DEF_COMMON("schur_exp_trans_sqdiff",
+                "(- (+ (% A B) (* s0 (exp C))) (t D)) ; (accu (square (- A B)))", 4, 2, 1,
+                FX_KIND_MULTI, ALL_DTYPES, false, false)
+  static constexpr const char* slots[] = {"A", "B", "C", "D", "Z", "s"};
+  static constexpr double defaults[] = {3.5};
+  template <class T> static FX_HD auto build(const double* s) {
+    auto A = in<0, T>(); auto B = in<1, T>(); auto C = in<2, T>(); auto D = in<3, T>();
+    return with_accu(A % B + s[0] * exp(C) - trans(D), square(A - B));
+  }
+};
+
 // Z = X % Y + sqrt(abs(W)) / (1 + exp(-V))
 struct SchurSqrtSigmoid {
   FX_DEF_COMMON("schur_sqrt_sigmoid", "(+ (% X Y) (/ (sqrt (abs W)) (+ s0 (exp (neg V)))))", 4,

@@ -90,6 +90,15 @@ struct OpGt {  // 1 where a > b, else 0 (the mask X > 0 of the relu expression)
   template <class C> static FX_D void d(C, C, C& da, C& db) { da = C(0); db = C(0); }
 };
 
+// The first of two values. Joins a stored tree and a second tree over the
+// same leaves into one node, so that one load of the leaves serves both
+// (the multi-output root WithAccu); the second value is read by the
+// epilogue from the same registers, not through this node.
+struct OpFirst {
+  template <class C> static FX_D C f(C a, C) { return a; }
+  template <class C> static FX_D void d(C, C, C& da, C& db) { da = C(1); db = C(0); }
+};
+
 struct OpNeg {
   template <class C> static FX_D C f(C a) { return -a; }
   template <class C> static FX_D C d(C, C) { return C(-1); }
@@ -255,6 +264,10 @@ template <class E> struct BRow : ExprBase { E e; };
 // name it; the fused kernels reject it (it must be materialised first).
 template <class L, class R> struct Prod : ExprBase { L l; R r; };
 
+// Two results over shared leaves (only at the root): Z = e, stored, and
+// s = accu(side), both from one pass over the union of their leaves.
+template <class E, class S> struct WithAccu : ExprBase { Bin<OpFirst, E, S> both; };
+
 // Terminal reductions (only at the root).
 template <class E> struct Accu : ExprBase { E e; };
 template <class E> struct Norm2 : ExprBase { E e; };
@@ -312,6 +325,9 @@ template <class A, one_expr<A> = 0> FX_HD Tr<A> trans(A a) { return {{}, a}; }
 template <class A, one_expr<A> = 0> FX_HD BCol<A> each_col(A a) { return {{}, a}; }
 template <class A, one_expr<A> = 0> FX_HD BRow<A> each_row(A a) { return {{}, a}; }
 
+template <class A, class B, both_expr<A, B> = 0> FX_HD WithAccu<A, B> with_accu(A a, B b) {
+  return {{}, {{}, a, b}};
+}
 template <class A, one_expr<A> = 0> FX_HD Accu<A> accu(A a) { return {{}, a}; }
 template <class A, one_expr<A> = 0> FX_HD Norm2<A> norm2(A a) { return {{}, a}; }
 template <int D, class A, one_expr<A> = 0> FX_HD SumDim<A, D> sum(A a) { return {{}, a}; }

@@ -185,6 +185,7 @@ template <class CT, int V> FX_D CT lane_sum(const CT (&v)[V]) {
 template <class T, int V> struct EpiStore {
   T* z;
   int64_t ldz;
+  static constexpr bool side_tree = false;
   static constexpr bool stores = true;
   static constexpr bool reduces = false;
   static constexpr bool pure_sum = false;
@@ -209,6 +210,7 @@ template <class T, int V> struct EpiStore {
 // Fused sum of the elements (SQ: of their squares, for the 2-norm).
 template <class CTy, int V, bool SQ> struct EpiSum {
   int64_t ldz;
+  static constexpr bool side_tree = false;
   static constexpr bool stores = false;
   static constexpr bool reduces = true;
   static constexpr bool pure_sum = true;  // k_flat may combine several vectors per add
@@ -239,6 +241,7 @@ template <class CTy, int V, bool SQ> struct EpiSum {
 template <class T, int V> struct EpiStoreSum {
   T* z;
   int64_t ldz;
+  static constexpr bool side_tree = false;
   static constexpr bool stores = true;
   static constexpr bool reduces = true;
   static constexpr bool pure_sum = false;
@@ -257,6 +260,117 @@ template <class T, int V> struct EpiStoreSum {
     }
   }
 };
+
+// Store one tree and sum a second tree over the same leaves (the root
+// with_accu(E, S): Z = E, s = accu(S)). put() stores E's values; put_side()
+// evaluates S lane by lane from the same register pack and adds it.
+template <class T, int V, class S> struct EpiStoreSide {
+  T* z;
+  int64_t ldz;
+  S side;
+  static constexpr bool side_tree = true;
+  static constexpr bool stores = true;
+  static constexpr bool reduces = true;
+  static constexpr bool pure_sum = false;
+  static constexpr bool sqrt_result = false;
+  using State = ThreadSum<compute_t<T>>;
+  template <class CT> FX_D void put(State&, int64_t off, const CT (&v)[V], int nvalid) const {
+    EpiStore<T, V> s{z, ldz};
+    typename EpiStore<T, V>::State d;
+    s.put(d, off, v, nvalid);
+  }
+  template <class LL, int VP, class CT>
+  FX_D void put_side(State& st, const Pack<LL, VP, CT>& p, int nvalid) const {
+    CT w[VP];
+#pragma unroll
+    for (int j = 0; j < VP; ++j) {
+      Ctx<LL, VP, CT> c{p, j};
+      w[j] = side.ev(c);
+    }
+    if (nvalid == VP) {
+      st.add(lane_sum(w));
+    } else {
+#pragma unroll
+      for (int j = 0; j < VP; ++j)
+        if (j < nvalid) st.add(w[j]);
+    }
+  }
+};
+
+// Hands lanes 0..nvalid-1 of v (and, for a side tree, the pack they came
+// from) to the epilogue.
+template <class Epi, class St, class CT, int V, class P>
+FX_D void epi_put(const Epi& epi, St& st, int64_t off, const CT (&v)[V], const P& p, int nvalid) {
+  epi.put(st, off, v, nvalid);
+  if constexpr (Epi::side_tree) epi.put_side(st, p, nvalid);
+}
+
+// ---------------------------------------------------------------- FP64 reduction helpers
+//
+// FP64 arithmetic is scarce on this part (about 1/64 of the FP32 rate), so
+// FP64 reductions spend as few FP64 instructions per element as they can:
+//  - a sum whose terms are products (a % b, square(a), the squares of a
+//    2-norm) folds the multiply into the accumulation, acc = fma(a, b, acc):
+//    one FP64 instruction per term instead of a multiply and an add, each
+//    term rounded once. Every lane of every unrolled vector keeps its own
+//    accumulator, so the chains are independent;
+//  - a maximum of absolute values compares IEEE bit patterns as signed
+//    64-bit integers (monotone for values with a clear sign bit; a NaN's
+//    pattern is above infinity's, so NaN still wins) on the integer units.
+
+template <class E> struct prod_root { static constexpr bool value = false; };
+template <class L, class R> struct prod_root<Bin<OpMul, L, R>> {
+  static constexpr bool value = true;
+  template <class Ctx, class CT>
+  static FX_D void parts(const Bin<OpMul, L, R>& e, const Ctx& c, CT& a, CT& b) {
+    a = e.l.ev(c);
+    b = e.r.ev(c);
+  }
+};
+template <class X> struct prod_root<Un<OpSquare, X>> {
+  static constexpr bool value = true;
+  template <class Ctx, class CT>
+  static FX_D void parts(const Un<OpSquare, X>& e, const Ctx& c, CT& a, CT& b) {
+    a = e.e.ev(c);
+    b = a;
+  }
+};
+
+// The two factors of term j of pack p: the root's operands, or for a sum of
+// squares (SQ) the value twice.
+template <bool SQ, class E, class LL, int V, class CT>
+FX_D void term_parts(const E& e, const Pack<LL, V, CT>& p, int j, CT& a, CT& b) {
+  Ctx<LL, V, CT> c{p, j};
+  if constexpr (SQ) {
+    a = e.ev(c);
+    b = a;
+  } else {
+    prod_root<E>::parts(e, c, a, b);
+  }
+}
+
+template <class E> struct abs_root { static constexpr bool value = false; };
+template <class X> struct abs_root<Un<OpAbs, X>> { static constexpr bool value = true; };
+
+// Running maximum: NaN-propagating compare, or (INT) signed 64-bit compares
+// of bit patterns of values known to have a clear sign bit.
+template <class CT, bool INT> struct MaxAcc {
+  CT m;
+  FX_D void init() { m = neg_inf<CT>(); }
+  FX_D void add(CT v) { m = max_nan(m, v); }
+  FX_D CT get() const { return m; }
+};
+template <> struct MaxAcc<double, true> {
+  long long m;
+  FX_D void init() { m = -1; }
+  FX_D void add(double v) {
+    const long long b = __double_as_longlong(v);
+    m = b > m ? b : m;
+  }
+  FX_D double get() const { return m < 0 ? neg_inf<double>() : __longlong_as_double(m); }
+};
+template <class E, class CT>
+using max_acc_t = MaxAcc<CT, std::is_same<CT, double>::value && abs_root<E>::value>;
 
 // ---------------------------------------------------------------- combines
 
@@ -363,8 +477,16 @@ __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const i
   const int64_t nv = n / V;
   const int64_t bdim = blockDim.x;
   const int64_t step = int64_t(gridDim.x) * bdim * U;
+  // FP64 sums of products: one fma per term into U x V accumulators
+  constexpr bool FMA64 = Epi::pure_sum && std::is_same<CT, double>::value &&
+                         (Epi::sqrt_result || prod_root<E>::value);
   typename Epi::State st;
   st.init();
+  CT facc[FMA64 ? U : 1][FMA64 ? V : 1];
+#pragma unroll
+  for (int u = 0; u < (FMA64 ? U : 1); ++u)
+#pragma unroll
+    for (int j = 0; j < (FMA64 ? V : 1); ++j) facc[u][j] = CT(0);
   for (int64_t b = int64_t(blockIdx.x) * bdim * U + threadIdx.x; b < nv; b += step) {
     Pack<LL, V, CT> p[U];
 #pragma unroll
@@ -379,7 +501,19 @@ __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const i
         load_flat(p[u], sl, vi * V, r, c);
       }
     }
-    if constexpr (Epi::pure_sum) {
+    if constexpr (FMA64) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (b + u * bdim < nv) {
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            CT x, y;
+            term_parts<Epi::sqrt_result>(e, p[u], j, x, y);
+            facc[u][j] = __fma_rn(x, y, facc[u][j]);
+          }
+        }
+      }
+    } else if constexpr (Epi::pure_sum) {
       // one compensated add per step: the U vectors' sums added pairwise
       CT vs[U];
 #pragma unroll
@@ -400,7 +534,7 @@ __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const i
         if (vi < nv) {
           CT v[V];
           eval_lanes<V>(e, p[u], v);
-          epi.put(st, vi * V, v, V);
+          epi_put(epi, st, vi * V, v, p[u], V);
         }
       }
     }
@@ -414,8 +548,16 @@ __global__ void __launch_bounds__(512) k_flat(const E e, const Slots sl, const i
       CT v[V];
 #pragma unroll
       for (int j = 0; j < V; ++j) v[j] = v1[0];
-      epi.put(st, i, v, 1);
+      epi_put(epi, st, i, v, q, 1);
     }
+  }
+  if constexpr (FMA64) {
+    CT w[U * V];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < V; ++j) w[u * V + j] = facc[u][j];
+    st.add(lane_sum(w));
   }
   if constexpr (Epi::reduces) finish_full_reduce<CT, Epi::sqrt_result>(st, red);
 }
@@ -569,7 +711,7 @@ FX_D void tile_body(const E& e, const Slots& sl, int64_t R, int64_t C, int64_t r
     if (c < C && nvalid > 0) {
       CT v[V];
       eval_lanes<V>(e, p[q], v);
-      epi.put(st, r + c * epi.ldz, v, nvalid);
+      epi_put(epi, st, r + c * epi.ldz, v, p[q], nvalid);
     }
   }
 }
@@ -604,13 +746,21 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
   using LL = leaves_t<E>;
   using CT = ct_of<E>;
   static_assert(G == 32 || G == NT, "a column is reduced by a warp or a block");
+  // FP64 sums of products: one fma per term into U x V accumulators
+  constexpr bool FMA64 = !ISMAX && std::is_same<CT, double>::value && prod_root<E>::value;
   constexpr int GPB = NT / G;
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
   for (int64_t cb = int64_t(blockIdx.x) * GPB; cb < C; cb += int64_t(gridDim.x) * GPB) {
     const int64_t c = cb + g;
     ThreadSum<CT> acc;
     acc.init();
-    CT m = neg_inf<CT>();
+    max_acc_t<E, CT> mx;
+    mx.init();
+    CT facc[FMA64 ? U : 1][FMA64 ? V : 1];
+#pragma unroll
+    for (int u = 0; u < (FMA64 ? U : 1); ++u)
+#pragma unroll
+      for (int j = 0; j < (FMA64 ? V : 1); ++j) facc[u][j] = CT(0);
     if (c < C) {
       for (int64_t rb = int64_t(lane) * V; rb < R; rb += int64_t(G) * V * U) {
         Pack<LL, V, CT> p[U];
@@ -619,6 +769,21 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
           const int64_t r = rb + int64_t(u) * G * V;
           const int nv = clamp_valid(R - r, V);
           if (nv > 0) load_rc(p[u], sl, r, c, nv);
+        }
+        if constexpr (FMA64) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int nv = clamp_valid(R - (rb + int64_t(u) * G * V), V);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+              if (j < nv) {
+                CT x, y;
+                term_parts<false>(e, p[u], j, x, y);
+                facc[u][j] = __fma_rn(x, y, facc[u][j]);
+              }
+            }
+          }
+          continue;
         }
         // sums: the U vectors' lanes are added pairwise into one value per
         // step, then one compensated add (short dependency chains, which
@@ -635,7 +800,7 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
             if (ISMAX) {
 #pragma unroll
               for (int j = 0; j < V; ++j)
-                if (j < nv) m = max_nan(m, v[j]);
+                if (j < nv) mx.add(v[j]);
             } else if (nv == V) {
               vs[u] = lane_sum(v);
             } else {
@@ -648,6 +813,15 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
         if (!ISMAX) acc.add(lane_sum(vs));
       }
     }
+    if constexpr (FMA64) {
+      CT w[U * V];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < V; ++j) w[u * V + j] = facc[u][j];
+      acc.add(lane_sum(w));
+    }
+    const CT m = mx.get();
     CT res;
     if constexpr (G == 32) {
       if (ISMAX) {
@@ -785,11 +959,11 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
   const int s = blockIdx.y;
   const int64_t cb = C * s / rr.S, ce = C * (s + 1) / rr.S;
   ThreadSum<CT> acc[V];
-  CT m[V];
+  max_acc_t<E, CT> mx[V];
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     acc[j].init();
-    m[j] = neg_inf<CT>();
+    mx[j].init();
   }
   if (nvalid > 0) {
     for (int64_t c = cb; c < ce; c += U) {
@@ -804,13 +978,16 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
           eval_lanes<V>(e, p[u], v);
 #pragma unroll
           for (int j = 0; j < V; ++j) {
-            if (ISMAX) m[j] = max_nan(m[j], v[j]);
+            if (ISMAX) mx[j].add(v[j]);
             else acc[j].add(v[j]);
           }
         }
       }
     }
   }
+  CT m[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) m[j] = mx[j].get();
   row_finish<ISMAX, V, CT>(rr, acc, m, R, r, nvalid, s, NT);
 }
 

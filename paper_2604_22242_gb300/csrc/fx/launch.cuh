@@ -525,6 +525,40 @@ template <class T, class E> fx_status run_multi(const Run& r, const E& e) {
       r, e, sl, R, C, vec, EpiStoreSum<T, V>{z, zb.ld}, EpiStoreSum<T, 1>{z, zb.ld}, red);
 }
 
+// with_accu(E, S): Z = E stored and s = accu(S), one pass over the union of
+// their leaves (the kernel's tree is Bin<OpFirst, E, S>; the epilogue sums S
+// from the same registers).
+template <class T, class Root> fx_status run_multi_side(const Run& r, const Root& root) {
+  using E = typename root_of<Root>::inner;   // Bin<OpFirst, E1, S>
+  using S = decltype(E::r);
+  using LL = leaves_t<E>;
+  constexpr int V = vec_width<E, 16>();
+  const E& e = inner_of(root);
+  const Binding& zb = r.b[r.n_in];
+  const Binding& sb = r.b[r.n_in + 1];
+  const int64_t R = zb.rows, C = zb.cols;
+  FX_TRY(check_leaves<LL>(r.b, R, C));
+  if (sb.rows * sb.cols != 1) return fail(FX_E_SHAPE, "the accu output must be 1 x 1");
+  const Slots sl = make_slots(r.b, r.n_in);
+  T* z = static_cast<T*>(zb.p);
+  RedArgs red{};
+  red.out = sb.p;
+  using EV = EpiStoreSide<T, V, S>;
+  using E1 = EpiStoreSide<T, 1, S>;
+  const bool zdense = zb.ld == R || C == 1;
+  if constexpr (count_mt<LL>() == 0) {
+    if (zdense && flat_ok<LL>(r.b, R, C, 1)) {
+      if (flat_ok<LL>(r.b, R, C, V) && leaves_flat<LL>(r.b, V * sizeof(T)) &&
+          aligned(z, V * sizeof(T)))
+        return launch_flat<E, EV, V>(r, e, sl, R * C, EV{z, R, e.r}, red, R);
+      return launch_flat<E, E1, 1>(r, e, sl, R * C, E1{z, R, e.r}, red, R);
+    }
+  }
+  const bool vec = leaves_vec<LL, V>(r.b) && aligned(z, V * sizeof(T)) && zb.ld % V == 0;
+  return launch_tiles<T, E, EV, E1, V>(r, e, sl, R, C, vec, EV{z, zb.ld, e.r},
+                                       E1{z, zb.ld, e.r}, red);
+}
+
 // ---------------------------------------------------------------- A5: accu, norm
 
 template <class T, class Root> fx_status run_full_reduce(const Run& r, const Root& root) {
@@ -654,13 +688,17 @@ template <class T, class Root> fx_status run_dim_reduce(const Run& r, const Root
 
 template <class T, class Root> fx_status run_root(const Run& r, const Root& root, int kind) {
   static_assert(!has_prod_v<Root>, "a matrix product is a fusion boundary");
+  if constexpr (is_with_accu<Root>::value) {
+    return run_multi_side<T>(r, root);
+  }
   if (kind == FX_KIND_MULTI) {
     if constexpr (root_of<Root>::kind == FX_KIND_ELEMENTWISE) return run_multi<T>(r, root);
     return fail(FX_E_UNSUPPORTED, "multi-output needs an element-wise tree");
   }
   if constexpr (root_of<Root>::kind == FX_KIND_ELEMENTWISE) return run_elementwise<T>(r, root);
   else if constexpr (root_of<Root>::kind == FX_KIND_FULL_REDUCE) return run_full_reduce<T>(r, root);
-  else return run_dim_reduce<T>(r, root);
+  else if constexpr (root_of<Root>::kind == FX_KIND_DIM_REDUCE) return run_dim_reduce<T>(r, root);
+  else return fail(FX_E_UNSUPPORTED, "unknown root");
 }
 
 // ---------------------------------------------------------------- A9: backward

@@ -14,6 +14,8 @@
 //      accu / norm root                                -> same, with a fused
 //                                                         reduction epilogue (A5)
 //      sum / max along a dimension                     -> dim reduction (A6)
+//      with_accu(E, S): Z = E and s = accu(S)           -> E's family, S summed
+//                                                         from the same registers
 //    A matrix product node is a fusion boundary (has_prod_v): gemm.cuh
 //    computes it first into a temporary, bound as a plain leaf of the rest.
 #pragma once
@@ -167,6 +169,13 @@ template <class E, int D> struct Norm<MaxDim<E, D>, false> {
   static FX_HD type make(const MaxDim<E, D>& x) { return {{}, Norm<E, false>::make(x.e)}; }
 };
 
+template <class E, class S> struct Norm<WithAccu<E, S>, false> {
+  using type = WithAccu<typename Norm<E, false>::type, typename Norm<S, false>::type>;
+  static FX_HD type make(const WithAccu<E, S>& x) {
+    return {{}, {{}, Norm<E, false>::make(x.both.l), Norm<S, false>::make(x.both.r)}};
+  }
+};
+
 template <class E> FX_HD typename Norm<E, false>::type normalize(const E& e) {
   return Norm<E, false>::make(e);
 }
@@ -179,7 +188,13 @@ template <class E> struct root_of<Norm2<E>> { static constexpr int kind = FX_KIN
 template <class E, int D> struct root_of<SumDim<E, D>> { static constexpr int kind = FX_KIND_DIM_REDUCE; using inner = E; };
 template <class E, int D> struct root_of<MaxDim<E, D>> { static constexpr int kind = FX_KIND_DIM_REDUCE; using inner = E; };
 
+template <class E, class S> struct root_of<WithAccu<E, S>> { static constexpr int kind = FX_KIND_MULTI; using inner = Bin<OpFirst, E, S>; };
+
+template <class E> struct is_with_accu { static constexpr bool value = false; };
+template <class E, class S> struct is_with_accu<WithAccu<E, S>> { static constexpr bool value = true; };
+
 template <class E> FX_HD const E& inner_of(const E& e) { return e; }
+template <class E, class S> FX_HD const Bin<OpFirst, E, S>& inner_of(const WithAccu<E, S>& e) { return e.both; }
 template <class E> FX_HD const E& inner_of(const Accu<E>& e) { return e.e; }
 template <class E> FX_HD const E& inner_of(const Norm2<E>& e) { return e.e; }
 template <class E, int D> FX_HD const E& inner_of(const SumDim<E, D>& e) { return e.e; }

@@ -282,7 +282,9 @@ __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl
           for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(v[j]);
           *reinterpret_cast<Raw<T, V>*>(zt + (r / G::IB) * G::BOX + swz<G::es>(r % G::IB, c)) = o;
         }
-        if constexpr (Epi::reduces) {
+        if constexpr (Epi::side_tree) {
+          epi.put_side(st, p, nvalid);
+        } else if constexpr (Epi::reduces) {
           if (nvalid == V) {
             CT w[V];
 #pragma unroll

@@ -163,7 +163,23 @@ fx_status run_unfused(fx_expr* x, const Root& root, int kind, cudaStream_t st,
   FX_TRY(x->ws_tmp.ensure(per * (ntmp > 0 ? ntmp : 1), st));
   UState u{r, R, C, sizeof(T), static_cast<char*>(x->ws_tmp.p), x->ws_tmp.bytes, 0};
   constexpr int rk = root_of<Root>::kind;
-  if constexpr (rk == FX_KIND_ELEMENTWISE) {
+  if constexpr (is_with_accu<Root>::value) {
+    // Z = E as its own chain of launches into Z, then S's chain into a
+    // temporary and accu over it (an eager library evaluates the two
+    // expressions one after the other)
+    const Binding& zb = r.b[r.n_in];
+    if (zb.rows != R || zb.cols != C) return fail(FX_E_SHAPE, "output shape differs from the tree's");
+    Binding z, v;
+    FX_TRY((Unf<T, decltype(e.l)>::run(u, e.l, z, &zb)));
+    FX_TRY((Unf<T, decltype(e.r)>::run(u, e.r, v, nullptr)));
+    Binding b3[2] = {v, r.b[r.n_in + 1]};
+    Run r3 = r;
+    r3.b = b3;
+    r3.n_in = 1;
+    using S = decltype(e.r);
+    using LV = Leaf<0, typename uview<S, T>::elem, uview<S, T>::mode>;
+    return run_full_reduce<T>(r3, Accu<LV>{});
+  } else if constexpr (rk == FX_KIND_ELEMENTWISE) {
     const Binding& zb = r.b[r.n_in];
     if (zb.rows != R || zb.cols != C) return fail(FX_E_SHAPE, "output shape differs from the tree's");
     Binding z;

@@ -33,6 +33,8 @@ TREES = {
     "absdiff_rowmax": "(max (abs (- X Y)) 1)",
     "diff_norm": "(norm (- X Y))",
     "schur_trans_accu": "(+ (% A B) (* {s0} (t C)))",
+    # two results over the same leaves: Z (this tree) and s (SIDE_SUM below)
+    "schur_exp_trans_sqdiff": "(- (+ (% A B) (* {s0} (exp C))) (t D))",
     "sigmoid_sqloss": "(accu (square (- (sigmoid (+ (% X W) (each_col b))) Y)))",
     "expr1": "(+ (* {s0} (+ (t X) Y)) (* {s0} (+ X (t Y))))",
     "expr2": "(+ (+ (* {s0} A) (t (+ B C))) (log (pow D {s1})))",
@@ -52,12 +54,15 @@ for _n in range(2, 17):
     for _k in range(2, _n + 1):
         _t = f"(+ {_t} A{_k})"
     TREES[f"add{_n}"] = _t
-DEFAULT_SCALARS = {"schur_exp_trans": [3.5], "schur_sqrt_sigmoid": [1.0],
+# the second tree of a two-result definition, summed into s
+SIDE_SUM = {"schur_exp_trans_sqdiff": "(accu (square (- A B)))"}
+DEFAULT_SCALARS = {"schur_exp_trans": [3.5], "schur_exp_trans_sqdiff": [3.5], "schur_sqrt_sigmoid": [1.0],
                    "schur_trans_accu": [0.5], "expr1": [2.0], "expr2": [0.75, 2.0], "relu": [0.0],
                    "sigmoid": [1.0], "swish": [1.0], "gelu": [0.7978845608028654, 0.044715],
                    "gemm_scale": [2.0], "gemm_epilogue": [0.5]}
 SLOTS = {
     "schur_exp_trans": ["A", "B", "C", "D"],
+    "schur_exp_trans_sqdiff": ["A", "B", "C", "D"],
     "sqdiff_accu": ["A", "B"],
     "schur_sqrt_sigmoid": ["X", "Y", "W", "V"],
     "schur_colsum": ["X", "Y"],
@@ -72,7 +77,7 @@ SLOTS = {
 }
 for _n in range(2, 17):
     SLOTS[f"add{_n}"] = [f"A{_k}" for _k in range(1, _n + 1)]
-TRANSPOSED = {"schur_exp_trans": {"D"}, "schur_trans_accu": {"C"}, "expr2": {"B", "C"}}
+TRANSPOSED = {"schur_exp_trans": {"D"}, "schur_exp_trans_sqdiff": {"D"}, "schur_trans_accu": {"C"}, "expr2": {"B", "C"}}
 VECTORS = {"sigmoid_sqloss": {"b"}}
 
 def tree_of(name, scalars=None):
@@ -256,6 +261,16 @@ def oracle_outputs(name, env, scalars=None, sample=None, scale="gate"):
         mg = oracle.evaluate_mag(t, env) if need_m else None
         return v, sg, mg
 
+    if name in SIDE_SUM:
+        res = {"Z": _pick(*elementwise(tree), scale, gate)}
+        side = SIDE_SUM[name]
+        sgate = gate_scale(side)
+        need_s = scale in ("both", "sigma") or (scale == "gate" and sgate == "sigma")
+        need_m = scale in ("both", "m") or (scale == "gate" and sgate == "m")
+        v, sg, mg = reduction(side)
+        res["s"] = _pick(v[0, 0], None if sg is None else sg[0, 0],
+                         None if mg is None else mg[0, 0], scale, sgate)
+        return res
     if name == "schur_trans_accu":
         res = {"Z": _pick(*elementwise(tree), scale, gate)}
         v, sg, mg = reduction(f"(accu {tree})")

@@ -14,10 +14,10 @@ from harness import (SLOTS, oracle_outputs, panel_report, record, run, scaled_er
 
 pytestmark = pytest.mark.gpu
 
-NAMES = ["schur_exp_trans", "sqdiff_accu", "schur_sqrt_sigmoid", "schur_colsum",
-         "absdiff_rowmax", "diff_norm", "schur_trans_accu", "sigmoid_sqloss"]
+NAMES = ["schur_exp_trans", "sqdiff_accu", "schur_exp_trans_sqdiff", "schur_sqrt_sigmoid",
+         "schur_colsum", "absdiff_rowmax", "diff_norm", "schur_trans_accu", "sigmoid_sqloss"]
 DIST = {"schur_exp_trans": "uniform", "sqdiff_accu": "uniform", "schur_trans_accu": "uniform",
-        "sigmoid_sqloss": "normal_half"}
+        "schur_exp_trans_sqdiff": "uniform", "sigmoid_sqloss": "normal_half"}
 SMALL = [(1, 1), (1, 7), (7, 1), (33, 17), (100, 37), (257, 129), (64, 64)]
 
 
@@ -76,7 +76,7 @@ def test_unfused_baseline_matches(fx, name, storage):
 
 
 @pytest.mark.parametrize("name", ["sqdiff_accu", "schur_colsum", "absdiff_rowmax", "diff_norm",
-                                  "schur_trans_accu", "sigmoid_sqloss"])
+                                  "schur_trans_accu", "sigmoid_sqloss", "schur_exp_trans_sqdiff"])
 def test_reductions_bitwise_repeatable(fx, name):
     R, C = 1000, 700
     env = env_for(name, "f32", R, C, seed=14)
@@ -104,7 +104,8 @@ def test_launch_shapes(fx, name, storage):
             check(name, storage, got, oracle_outputs(name, env), f" at {R}x{C} shape {shape}")
 
 
-@pytest.mark.parametrize("name", ["schur_exp_trans", "schur_trans_accu", "absdiff_rowmax"])
+@pytest.mark.parametrize("name", ["schur_exp_trans", "schur_trans_accu", "absdiff_rowmax",
+                                  "schur_exp_trans_sqdiff"])
 def test_kernel_variants_agree_bitwise(fx, name):
     """Every variant evaluates an element with the same operations, so the
     element-wise outputs and the row maxima agree bit for bit."""
@@ -125,7 +126,7 @@ TMA_SHAPES = {"f32": [(1000, 700), (972, 712), (64, 64)], "bf16": [(1000, 712), 
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
-@pytest.mark.parametrize("name", ["schur_exp_trans", "schur_trans_accu"])
+@pytest.mark.parametrize("name", ["schur_exp_trans", "schur_trans_accu", "schur_exp_trans_sqdiff"])
 def test_tma_tiles(fx, name, storage):
     for k, (R, C) in enumerate(TMA_SHAPES[storage]):
         env = env_for(name, storage, R, C, seed=40 + k)
@@ -209,8 +210,25 @@ def full_check(fx, name, storage, env, R, C, label):
 def test_workload_1024_f32(fx):
     R = C = 1024
     env = synth.operands(0, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], "f32", "uniform")
-    for name in ("schur_exp_trans", "sqdiff_accu"):
+    for name in ("schur_exp_trans_sqdiff", "schur_exp_trans", "sqdiff_accu"):
         full_check(fx, name, "f32", env, R, C, " at 1024^2")
+
+
+def test_two_results_match_the_separate_trees(fx):
+    """Z and s of the one-pass definition are bit for bit those of the two
+    separate trees: Z's elements take the same operations, and the sum runs
+    over the same values (the launch shapes are fixed alike; the grids, and
+    so the partial sums' grouping, can differ, so s is held to the
+    reduction bound instead)."""
+    R, C = 1000, 712
+    env = synth.operands(3, [("A", R, C), ("B", R, C), ("C", R, C), ("D", C, R)], "f32", "uniform")
+    for pipe in (0, 1, 2):
+        both = run(fx, "schur_exp_trans_sqdiff", "f32", env, R, C, shape=(256, 4, 0, pipe))
+        z = run(fx, "schur_exp_trans", "f32", env, R, C, shape=(256, 4, 0, pipe))
+        s = run(fx, "sqdiff_accu", "f32", env, R, C, shape=(256, 4, 0, pipe))
+        assert np.array_equal(both["Z"], z["Z"]), pipe
+        assert abs(both["s"] - s["s"]) <= 1e-6 * abs(s["s"]), pipe
+        assert both["_launches"] == 1
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
@@ -237,8 +255,7 @@ def test_workload_16384(fx, env16384):
     storage, env = env16384
     R = C = 16384
     reps = {}
-    for name in ("schur_exp_trans", "sqdiff_accu"):
-        reps.update(full_check(fx, name, storage, env, R, C, " at 16384^2"))
+    reps.update(full_check(fx, "schur_exp_trans_sqdiff", storage, env, R, C, " at 16384^2"))
     # 3.5 exp(C) passes the FP16 maximum (65504) for C > 9.84: such outputs
     # must be infinities of the oracle's sign (checked above); there are some
     over = reps["Z"].overflow
@@ -256,5 +273,5 @@ def test_workload_16384_clamped(fx, env16384):
     vals = synth.to_f64(c.data, storage)
     clamped = synth.Buffer(np.where(vals > 9.0, cap, c.data), c.rows, c.cols, c.ld, storage)
     env2 = dict(env, C=clamped)
-    rep = full_check(fx, "schur_exp_trans", storage, env2, R, C, " at 16384^2, C <= 9")["Z"]
+    rep = full_check(fx, "schur_exp_trans_sqdiff", storage, env2, R, C, " at 16384^2, C <= 9")["Z"]
     assert rep.overflow == 0
