@@ -281,11 +281,12 @@ struct GemmScale {
   }
 };
 
-// A product with an element-wise remainder: the GEMM, then one fused pass
-// Z = sigmoid(s0 * (X * Y) + W)
+// A product with an element-wise remainder, Z = sigmoid(s0 * (X * Y) + W):
+// for BF16/FP16 one tensor-core kernel evaluates the remainder from the
+// accumulator; otherwise the GEMM, then one fused pass
 struct GemmEpilogue {
   FX_DEF_COMMON("gemm_epilogue", "(sigmoid (+ (* s0 (* X Y)) W))", 3, 1, 1, FX_KIND_ELEMENTWISE,
-                dmask(FX_F32) | dmask(FX_BF16) | dmask(FX_F64), false, false)
+                ALL_DTYPES, false, false)
   static constexpr const char* slots[] = {"X", "Y", "W", "Z"};
   static constexpr double defaults[] = {0.5};
   template <class T> static FX_HD auto build(const double* s) {

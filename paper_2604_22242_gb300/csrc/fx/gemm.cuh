@@ -18,6 +18,7 @@
 
 #include <cublas_v2.h>
 
+#include "umma.cuh"
 #include "unfused.cuh"
 
 namespace fx {
@@ -274,6 +275,80 @@ template <class L, class R> struct ScaledProd<SL<OpMul, Prod<L, R>>> {
   static const P& prod(const SL<OpMul, P>& e) { return e.e; }
 };
 
+// ---------------------------------------------------------------- tcgen05 path
+
+// Trees the tensor-core kernel takes: BF16 or FP16 storage, one matrix
+// product of two matrix leaves (plain or transposed), and an element-wise
+// remainder whose other leaves are plain matrices of the storage type.
+template <class T, int NIN, class Root> struct umma_ok {
+  static constexpr bool value = [] {
+    if constexpr (!(std::is_same<T, bf16>::value || std::is_same<T, f16>::value)) {
+      return false;
+    } else if constexpr (root_of<Root>::kind != FX_KIND_ELEMENTWISE || !has_prod_v<Root>) {
+      return false;
+    } else if constexpr (Lift<Root, T, NIN>::count != 1) {
+      return false;
+    } else {
+      using P = typename the_prod<Root>::type;
+      return prod_of_leaves<P>::value &&
+             others_plain<leaves_t<typename Lift<Root, T, NIN>::type>, NIN, T>();
+    }
+  }();
+};
+
+// Evaluates the whole tree with umma::k_gemm_umma when the operands allow
+// TMA (16-byte aligned bases and leading dimensions) and the shapes agree;
+// *used is false otherwise (the caller takes the library-GEMM path, which
+// also reports shape errors).
+template <class T, int NIN, class Root>
+fx_status run_umma(fx_expr* x, const Root& root, cudaStream_t st, bool* used) {
+  *used = false;
+  using LR = Lift<Root, T, NIN>;
+  using Lifted = typename LR::type;
+  constexpr int PS = NIN;
+  using P = typename the_prod<Root>::type;
+  using OA = Operand<std::decay_t<decltype(std::declval<P>().l)>>;
+  using OB = Operand<std::decay_t<decltype(std::declval<P>().r)>>;
+  constexpr bool AMN = !OA::trans, BMN = OB::trans;
+  const Binding& a = x->b[OA::slot];
+  const Binding& b = x->b[OB::slot];
+  const Binding& zb = x->b[NIN];
+  if (!a.bound || !b.bound || !zb.bound) return FX_OK;
+  const int64_t M = OA::trans ? a.cols : a.rows, Ka = OA::trans ? a.rows : a.cols;
+  const int64_t Kb = OB::trans ? b.cols : b.rows, N = OB::trans ? b.rows : b.cols;
+  if (Ka != Kb || zb.rows != M || zb.cols != N || M == 0 || N == 0 || Ka == 0) return FX_OK;
+  const int64_t lim = int64_t(1) << 31;
+  if (M >= lim || N >= lim || Ka >= lim || (N + umma::BN - 1) / umma::BN > 65535) return FX_OK;
+  Binding bt[FX_MAX_SLOTS];
+  for (int k = 0; k < NIN; ++k) bt[k] = x->b[k];
+  bt[PS] = Binding{nullptr, M, N, M, true};
+  if (check_leaves<leaves_t<Lifted>>(bt, M, N) != FX_OK) {
+    cudaGetLastError();
+    return FX_OK;  // the library-GEMM path reports the shape error
+  }
+  CUtensorMap ma, mb;
+  const bool oka = AMN ? encode_map<T>(&ma, a.p, M, Ka, a.ld, 64, 64)
+                       : encode_map<T>(&ma, a.p, Ka, M, a.ld, 64, umma::BM);
+  const bool okb = BMN ? encode_map<T>(&mb, b.p, N, Ka, b.ld, 64, 64)
+                       : encode_map<T>(&mb, b.p, Ka, N, b.ld, 64, umma::BN);
+  if (!oka || !okb) return FX_OK;
+  auto kern = umma::k_gemm_umma<T, AMN, BMN, Lifted, PS>;
+  const int smem = umma::NS * umma::STAGE + 1024 + int(sizeof(umma::Bars));
+  FX_TRY(allow_smem(kern, smem));
+  FX_TRY(x->ws_err.ensure(256, st));
+  unsigned int* err = static_cast<unsigned int*>(x->ws_err.p);
+  const Slots sl = make_slots(x->b, NIN);
+  const dim3 grid(unsigned((M + umma::BM - 1) / umma::BM), unsigned((N + umma::BN - 1) / umma::BN));
+  *used = true;
+  x->last_launches = 0;
+  kern<<<grid, 192, smem, st>>>(ma, mb, LR::make(root), sl, static_cast<T*>(zb.p), zb.ld, int(M),
+                                int(N), int(Ka), err);
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return cuda_fail(le, "k_gemm_umma");
+  x->last_launches = 1;
+  return FX_OK;
+}
+
 // A tree with matrix products: products into temporaries (slots NIN ..
 // NIN+P-1 of a private binding table), then the lifted tree on the fused
 // path (or, for the unfused baseline, one launch per operator).
@@ -285,6 +360,15 @@ fx_status run_with_prods(fx_expr* x, const Root& root, int kind, cudaStream_t st
   static_assert(NIN + P + 2 <= FX_MAX_SLOTS, "too many matrix products in one tree");
   using Inner = typename root_of<Root>::inner;
   const Inner& inner = inner_of(root);
+  if constexpr (umma_ok<T, NIN, Root>::value) {
+    // launch-shape pipeline 0: the tensor-core kernel with the remainder in
+    // its epilogue; 1 and 2: the library GEMM and the fused pass
+    if (!unfused && kind == FX_KIND_ELEMENTWISE && x->tune.pipe == 0) {
+      bool used = false;
+      FX_TRY((run_umma<T, NIN>(x, root, st, &used)));
+      if (used) return FX_OK;
+    }
+  }
   Binding bb[FX_MAX_SLOTS];
   for (int k = 0; k < NIN; ++k) bb[k] = x->b[k];
   for (int j = 0; j < n_out; ++j) bb[NIN + P + j] = x->b[NIN + j];
