@@ -26,11 +26,15 @@ no flush between iterations.
 
   prec16384_f16_clamped   prec16384_f16's Z with C's values capped at 9 (every
                  FP16 output finite)
+  gemm8192_bf16 / gemm8192_f16   Z = sigmoid(X*Y/sqrt(K) + W) and Z = 2*X*Y^T at
+                 M = N = K = 8192 on the tensor-core kernel (TFLOP/s), beside
+                 the library GEMM plus the fused pass
 
 With no flags, the line also carries "errors" (every output of the step
 against the FP64 oracle, after the timed region) and "configs": each of
 small1024, expr8192_f64, prec16384_bf16, prec16384_f16,
-prec16384_f16_clamped, batch4096, loss8192_f32 and loss8192_bf16 measured
+prec16384_f16_clamped, batch4096, loss8192_f32, loss8192_bf16, gemm8192_bf16
+and gemm8192_f16 measured
 the same way (autotuned, --config-steps timed steps), with its GB/s,
 roofline fraction, speedup over the unfused baseline and errors.
 
@@ -103,6 +107,16 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def measured_tensor_peak():
+    """Dense BF16 tensor throughput (TFLOP/s) measured on this machine (burst: a
+    kernel timed alone), else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -160,11 +174,13 @@ class Clocks:
 # ---------------------------------------------------------------- workloads
 
 class Op:
-    """One fused evaluation: a launch, its unfused twin, and its algorithmic bytes."""
+    """One fused evaluation: a launch, its unfused twin, its algorithmic bytes
+    and (trees with a matrix product) its algorithmic flops."""
 
-    def __init__(self, key, nbytes, launch, unfused=None, launches=None):
+    def __init__(self, key, nbytes, launch, unfused=None, launches=None, flops=0):
         self.key, self.bytes, self.launch, self.unfused, self.launches = (
             key, nbytes, launch, unfused, launches)
+        self.flops = flops
 
 
 def _bind(fx, h, k, t, rows, cols, ld):
@@ -297,7 +313,69 @@ def workload(name, fx, torch, dev, sp, keep, size=8192, count=4096):
         return _expr_ops(fx, torch, dev, sp, trees, "f32", env, R, C, keep), cfg, "add16", False, "f32"
     if name in ("loss8192_f32", "loss8192_bf16"):
         return loss_workload(fx, torch, dev, sp, keep, name.split("_")[1], size)
+    if name in ("gemm8192_bf16", "gemm8192_f16"):
+        return gemm_workload(fx, torch, dev, sp, keep, name.split("_")[1], size)
     raise SystemExit(f"unknown workload {name}")
+
+
+def gemm_workload(fx, torch, dev, sp, keep, storage, size=8192):
+    """Trees with one matrix product at M = N = K = size: Z = sigmoid(s X Y + W)
+    (s = 1/sqrt(K), so the sigmoid is not saturated) and Fig. 1's Z = 2 X Y^T,
+    on the tcgen05 kernel with the remainder in its epilogue (launch-shape
+    pipeline 0); the same trees through the library GEMM and the fused pass
+    (pipeline 2) are timed beside them."""
+    import numpy as np
+    import synth
+    M = N = K = size
+    env = synth.operands(7, [("X", M, K), ("Y", K, N), ("W", M, N), ("Yt", N, K)], storage,
+                         "normal")
+    code = fx.FX_BF16 if storage == "bf16" else fx.FX_F16
+    tdt = torch.bfloat16 if storage == "bf16" else torch.float16
+    d = {}
+    for k, b in env.items():
+        t = torch.from_numpy(b.data.view(np.int16)).view(tdt) if storage == "bf16" else \
+            torch.from_numpy(b.data)
+        d[k] = t.to(dev)
+    keep["inputs"] = d
+    keep["env"] = env
+    flops = 2 * M * N * K
+    trees = [("gemm_epilogue", "epilogue", ["X", "Y", "W"], [1.0 / K ** 0.5]),
+             ("gemm_scale", "scale", ["X", "Yt"], [2.0])]
+
+    def make(pipe, suffix, check):
+        ops = []
+        for name, key, ins, scal in trees:
+            h = fx.fx_expr_create(name, code)
+            for i, v in enumerate(scal):
+                fx.fx_expr_set_scalar(h, i, v)
+            nb = 0
+            for k, sname in enumerate(ins):
+                b = env[sname]
+                fx.fx_expr_bind(h, k, d[sname].data_ptr(), b.rows, b.cols, b.ld)
+                nb += b.rows * b.cols * 2
+            z = torch.empty(M * N, dtype=tdt, device=dev)
+            fx.fx_expr_bind(h, len(ins), z.data_ptr(), M, N, M)
+            nb += M * N * 2
+            fx.fx_expr_set_launch_shape(h, 256, 4, 0, pipe)
+            keep[key + suffix] = (h, z)
+            keep.setdefault("_handles", []).append(h)
+            if check:
+                keep.setdefault("gemm_checks", []).append((name, key, ins, scal))
+            ops.append(Op(key + suffix, nb, (lambda h=h: fx.fx_eval(h, sp)),
+                          (lambda h=h: fx.fx_eval_unfused(h, sp)),
+                          (lambda h=h: fx.fx_expr_last_launches(h)), flops=flops))
+        return ops
+
+    ops = make(0, "", True)
+    keep["alt_ops"] = make(2, "_library", False)
+    keep["alt_what"] = ("the same trees through the library GEMM (cuBLAS) and the fused "
+                        "element-wise pass (launch-shape pipeline 2)")
+    keep["no_tune"] = True
+    cfg = {"workload": f"Z=sigmoid(X*Y/sqrt(K)+W) and Z=2*X*Y^T at M=N=K={size} {storage}",
+           "rows": M, "cols": N, "inner": K,
+           "inputs": "X, Y, W, Y^T-operand N(0,1), seed 7, column-major",
+           "l2": "operands 128 MiB each; a GEMM re-reads them from L2 by design, no flush"}
+    return ops, cfg, "epilogue", False, storage
 
 
 def batch_workload(fx, torch, dev, sp, keep, count=4096):
@@ -540,6 +618,7 @@ def oracle_errors(keep, storage, n_sample=1 << 16):
     import torch
 
     import oracle
+    import synth
     from oracle import grad as ograd
     from oracle.compare import TOL_TRANS, ErrorReport, gate_scale, tolerance
 
@@ -584,6 +663,37 @@ def oracle_errors(keep, storage, n_sample=1 << 16):
                 return ErrorReport(rst, tolerance(tree, storage), gate_scale(tree)).add(
                     g, v.ravel(), sg.ravel(), m.ravel())
             jobs[key] = rjob
+    for name, key, ins, scal in keep.get("gemm_checks", []):
+        _, z = keep[key]
+        tree = {"gemm_epilogue": "(sigmoid (+ (* {s0} (* X Y)) W))",
+                "gemm_scale": "(* {s0} (* X (t Y)))"}[name].format(s0=repr(float(scal[0])))
+        X = env[ins[0]]
+        M = X.rows
+        N = env[ins[2]].cols if name == "gemm_epilogue" else env[ins[1]].rows
+        rng = np.random.default_rng(17)
+        rs = np.sort(rng.choice(M, 64, replace=False))
+        cs = np.sort(rng.choice(N, 64, replace=False))
+        g = _host64(z.view(N, M).T[torch.from_numpy(rs).to(z.device)][:, torch.from_numpy(cs).to(
+            z.device)])
+
+        def sub(b, rows_, cols_):
+            full = b.data.reshape(b.cols, b.ld).T[: b.rows, :]
+            part = np.ascontiguousarray(full[rows_][:, cols_].T).ravel()
+            return synth.Buffer(part, len(rows_), len(cols_), len(rows_), b.storage)
+
+        K_ = X.cols
+        allk = np.arange(K_)
+        if name == "gemm_epilogue":
+            senv = {"X": sub(X, rs, allk), "Y": sub(env[ins[1]], allk, cs),
+                    "W": sub(env[ins[2]], rs, cs)}
+        else:
+            senv = {"X": sub(X, rs, allk), "Y": sub(env[ins[1]], cs, allk)}
+
+        def gjob(tree=tree, senv=senv, g=g):
+            v, sg = oracle.evaluate_sigma(tree, senv)
+            m = oracle.evaluate_mag(tree, senv)
+            return ErrorReport(storage, tolerance(tree, storage), gate_scale(tree)).add(g, v, sg, m)
+        jobs[key] = gjob
     if "loss" in keep:
         tree = ORACLE_OF["sigmoid_sqloss"]
         _, L, grads, _ = keep["loss"]
@@ -759,7 +869,8 @@ def release(fx, torch, keep):
 
 # the other measured configurations, reported in the default line's "configs"
 EXTRA_CONFIGS = ["small1024", "expr8192_f64", "prec16384_bf16", "prec16384_f16",
-                 "prec16384_f16_clamped", "batch4096", "loss8192_f32", "loss8192_bf16"]
+                 "prec16384_f16_clamped", "batch4096", "loss8192_f32", "loss8192_bf16",
+                 "gemm8192_bf16", "gemm8192_f16"]
 
 
 def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
@@ -769,7 +880,8 @@ def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
     keep = {}
     ops, cfg, dom, flush, storage = workload(name, fx, torch, dev, sp, keep, 8192, args.count)
     try:
-        handles = tune_workload(fx, args, keep, ops, cfg, sp)
+        if not keep.get("no_tune"):
+            tune_workload(fx, args, keep, ops, cfg, sp)
         flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
 
         def fl():
@@ -783,17 +895,21 @@ def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
             if keep.get("alt_ops"):
                 aops = keep["alt_ops"]
                 for h in [keep[o.key][0] for o in aops]:
-                    if not args.no_tune and not args.shape:
+                    if not args.no_tune and not args.shape and not keep.get("no_tune"):
                         fx.fx_tune(h, "search", sp)
                 a_all, a_ms, _, _, _ = timed_steps(torch, stream, aops, K, W, fl)
                 if flush:
                     a_ms = K * sum(statistics.mean(v) for v in a_all.values())
                 a_bytes = sum(o.bytes for o in aops)
-                alt = {"what": "the same results from separate trees, one launch each",
+                alt = {"what": keep.get("alt_what",
+                                        "the same results from separate trees, one launch each"),
                        "ms_per_step": round(a_ms / K, 4), "bytes_per_step": a_bytes,
                        "launches_per_step": len(aops),
                        "gbs": round(a_bytes * K / (a_ms / 1e3) / 1e9, 2),
                        "per_op_ms": {k: round(statistics.mean(v), 4) for k, v in a_all.items()}}
+                a_flops = sum(o.flops for o in aops)
+                if a_flops:
+                    alt["tflops"] = round(a_flops * K / (a_ms / 1e3) / 1e12, 1)
         per_ms = {k: statistics.mean(v) for k, v in per_all.items()}
         if flush:
             ms = K * sum(per_ms.values())
@@ -818,8 +934,23 @@ def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
             "inputs": cfg.get("inputs"),
         }
         refresh_outputs(torch, ops)
+        flops = sum(o.flops for o in ops)
+        if flops:
+            tpeak, tkind = measured_tensor_peak()
+            t_dom = dom_op.flops / (per_ms[dom] / 1e3) / 1e12
+            out["value"] = round(flops * K / (ms / 1e3) / 1e12, 1)
+            out["unit"] = "TFLOP/s"
+            out.pop("pct_of_peak", None)
+            out["roofline"] = {"bound": "tensor", "kernel": dom, "achieved": round(t_dom, 1),
+                               "peak": tpeak, "peak_kind": tkind + " (bf16 dense, burst)",
+                               "unit": "TFLOP/s", "frac": round(t_dom / tpeak, 4),
+                               "alg_flops_per_launch": dom_op.flops,
+                               "avg_launch_ms": round(per_ms[dom], 4)}
+            for k in out["per_op"]:
+                o = next(o for o in ops if o.key == k)
+                out["per_op"][k]["tflops"] = round(o.flops / (per_ms[k] / 1e3) / 1e12, 1)
         if alt:
-            out["separate_trees"] = alt
+            out["separate_trees" if not flops else "library_gemm"] = alt
         if (name, dom) in FP64_PIPE_OPS:
             alu = fp64_roofline(fx, sp, name, dom, dom_op, per_ms[dom], peak, storage, cfg)
             if alu:
@@ -844,7 +975,7 @@ def run_ours(args, rank, world):
     keep = {}
     ops, cfg, dom, flush, storage = workload(args.workload, fx, torch, dev, sp, keep, args.size,
                                             args.count)
-    handles = tune_workload(fx, args, keep, ops, cfg, sp)
+    handles = {} if keep.get("no_tune") else tune_workload(fx, args, keep, ops, cfg, sp)
     flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
     torch.cuda.synchronize()
     step_bytes = sum(o.bytes for o in ops)
@@ -1018,7 +1149,8 @@ def main():
     ap.add_argument("--workload", default="expr8192",
                     choices=["expr8192", "expr8192_f64", "small1024", "prec16384_bf16",
                              "prec16384_f16", "prec16384_f16_clamped", "batch4096",
-                             "loss8192_f32", "loss8192_bf16", "suite10k"])
+                             "loss8192_f32", "loss8192_bf16", "suite10k", "gemm8192_bf16",
+                             "gemm8192_f16"])
     ap.add_argument("--size", type=int, default=8192,
                     help="rows = cols of the expr8192 and loss8192 workloads (other values than "
                          "8192 also resize prec16384_* and suite10k, for profiling)")

@@ -318,7 +318,9 @@ fx_status run_umma(fx_expr* x, const Root& root, cudaStream_t st, bool* used) {
   const int64_t Kb = OB::trans ? b.cols : b.rows, N = OB::trans ? b.rows : b.cols;
   if (Ka != Kb || zb.rows != M || zb.cols != N || M == 0 || N == 0 || Ka == 0) return FX_OK;
   const int64_t lim = int64_t(1) << 31;
-  if (M >= lim || N >= lim || Ka >= lim || (N + umma::BN - 1) / umma::BN > 65535) return FX_OK;
+  if (M >= lim || N >= lim || Ka >= lim ||
+      ((M + umma::BM - 1) / umma::BM) * ((N + umma::BN - 1) / umma::BN) >= lim)
+    return FX_OK;
   Binding bt[FX_MAX_SLOTS];
   for (int k = 0; k < NIN; ++k) bt[k] = x->b[k];
   bt[PS] = Binding{nullptr, M, N, M, true};
@@ -338,7 +340,9 @@ fx_status run_umma(fx_expr* x, const Root& root, cudaStream_t st, bool* used) {
   FX_TRY(x->ws_err.ensure(256, st));
   unsigned int* err = static_cast<unsigned int*>(x->ws_err.p);
   const Slots sl = make_slots(x->b, NIN);
-  const dim3 grid(unsigned((M + umma::BM - 1) / umma::BM), unsigned((N + umma::BN - 1) / umma::BN));
+  const int64_t ntiles = ((M + umma::BM - 1) / umma::BM) * ((N + umma::BN - 1) / umma::BN);
+  const int sms = device_sms() > 0 ? device_sms() : 1;
+  const unsigned grid = unsigned(ntiles < sms ? ntiles : sms);   // persistent: one CTA per SM
   *used = true;
   x->last_launches = 0;
   kern<<<grid, 192, smem, st>>>(ma, mb, LR::make(root), sl, static_cast<T*>(zb.p), zb.ld, int(M),

@@ -11,17 +11,24 @@
 // lifted tree, in which P is a leaf - element by element, reading the other
 // leaves (W) from global memory and writing Z once.
 //
-// Per CTA (192 threads, one CTA per SM):
+// Persistent: one CTA of 192 threads per SM walks the output tiles (in
+// groups of 16 tile rows, for L2 reuse of the operands):
 //   warp 0      lane 0 loads the operand tiles with TMA (cp.async.bulk.tensor,
 //               128-byte swizzle) into a ring of NS shared-memory stages,
 //               one mbarrier per stage counting the bytes in ("full");
-//   warp 1      allocates the TMEM accumulator (256 columns); lane 0 issues,
-//               per 64-deep K step, four tcgen05.mma (M 128, N 256, K 16)
-//               and commits them to the stage's "empty" mbarrier (the stage
-//               is free again when they have read it), and after the last
-//               step commits to "acc" (the accumulator is complete);
-//   warps 2..5  wait for "acc", load their 32 TMEM lanes (rows) 32 columns at
-//               a time (tcgen05.ld 32x32b), evaluate the remainder and store.
+//   warp 1      allocates the TMEM (512 columns: two accumulators); lane 0
+//               issues, per 64-deep K step, four tcgen05.mma (M 128, N 256,
+//               K 16) into the tile's accumulator and commits them to the
+//               stage's "empty" mbarrier (the stage is free again when they
+//               have read it); after the tile's last step it commits to the
+//               accumulator's "full" barrier, and before reusing an
+//               accumulator it waits until the epilogue has read it out;
+//   warps 2..5  wait for a tile's accumulator, load their 32 TMEM lanes
+//               (rows) 16 columns at a time (tcgen05.ld 32x32b), release the
+//               accumulator after the last load, evaluate the remainder and
+//               store - while the next tile is multiplied into the other
+//               accumulator. The other leaves' values for the next 16
+//               columns are loaded before the current ones are computed.
 //
 // Operand layouts: column-major storage makes an operand K-major (K
 // contiguous) when it is read transposed or is the right factor, and
@@ -49,7 +56,7 @@ constexpr int SA = BM * BK * 2;       // A tile of one stage (16 KB)
 constexpr int SB = BN * BK * 2;       // B tile of one stage (32 KB)
 constexpr int STAGE = SA + SB;
 constexpr int NS = 4;                 // stages
-constexpr uint32_t TMEM_COLS = 256;   // FP32 accumulator: 128 lanes x 256 columns
+constexpr uint32_t TMEM_COLS = 512;   // two FP32 accumulators of 128 lanes x 256 columns
 
 // Shared-memory matrix descriptor (sm_100 family): start address, leading
 // and stride byte offsets (all >> 4), the fixed version bits 46-48 = 0b001,
@@ -99,16 +106,14 @@ FX_D void commit(uint64_t* bar) {
 }
 FX_D void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 FX_D void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// 32 consecutive FP32 columns of this thread's TMEM lane (warp-wide).
-FX_D void ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp-wide).
+FX_D void ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
 }
@@ -116,10 +121,10 @@ FX_D void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"
 
 // Element context of the epilogue: the product leaf (slot PS) is the FP32
 // accumulator; every other leaf is a plain matrix leaf whose values for the
-// thread's 32 columns were loaded into vals[leaf index][column].
-template <class LL, int PS> struct ECtx {
+// thread's CW columns were loaded into w[leaf index][column].
+template <class LL, int PS, class T, int CW> struct ECtx {
   using CT = float;
-  const float (*vals)[32];
+  const T (*w)[CW];
   float acc;
   int j;
   template <int K, int M> FX_D float leaf() const {
@@ -127,37 +132,68 @@ template <class LL, int PS> struct ECtx {
       return acc;
     } else {
       static_assert(M == MN, "the remainder's other leaves are plain matrices");
-      return vals[tl_index<LL, K, M>::value][j];
+      return to_compute<float>(w[tl_index<LL, K, M>::value][j]);
     }
   }
 };
 
-// vals[I][j] = leaf I at (m, n0 + j), j < nn (plain leaves other than PS).
-template <class LL, int PS, int I = 0>
-FX_D void load_others(float (*vals)[32], const Slots& sl, int64_t m, int64_t n0, int nn) {
+// An ordered 2-byte load (volatile, memory clobber): the epilogue's loads
+// of the next chunk are issued before the current chunk is computed and
+// stored, and the compiler may not sink them next to their use.
+template <class TL> FX_D TL ld_ordered(const TL* p) {
+  static_assert(sizeof(TL) == 2, "16-bit leaves");
+  unsigned short v;
+  asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+  TL r;
+  *reinterpret_cast<unsigned short*>(&r) = v;
+  return r;
+}
+
+// w[I][j] = leaf I at (m, n0 + j), j < nn (plain leaves other than PS).
+template <class LL, int PS, class T, int CW, int I = 0>
+FX_D void load_others(T (*w)[CW], const Slots& sl, int64_t m, int64_t n0, int nn) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
     if constexpr (L::slot != PS) {
-      using TL_ = typename L::elem;
       const SlotView& s = sl.s[L::slot];
-      const TL_* p = static_cast<const TL_*>(s.p) + m + n0 * s.ld;
+      const T* p = static_cast<const T*>(s.p) + m + n0 * s.ld;
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        vals[I][j] = j < nn ? to_compute<float>(sload(p + int64_t(j) * s.ld)) : 0.0f;
+      for (int j = 0; j < CW; ++j)
+        if (j < nn) w[I][j] = ld_ordered(p + int64_t(j) * s.ld);
     }
-    load_others<LL, PS, I + 1>(vals, sl, m, n0, nn);
+    load_others<LL, PS, T, CW, I + 1>(w, sl, m, n0, nn);
   }
 }
 
 struct Bars {
   uint64_t full[NS];
   uint64_t empty[NS];
-  uint64_t acc;
+  uint64_t accf[2];   // accumulator buffer b complete (MMA commit)
+  uint64_t acce[2];   // accumulator buffer b read out (one arrival per epilogue warp)
+  uint64_t drain;     // every MMA of the CTA complete (before the TMEM is freed)
   uint32_t taddr;
   volatile int abort;
 };
 
-// Z (M x N, column-major, ldz) = E(P) with P = op(A) op(B) of K terms.
+// Tile t of a tiles_m x tiles_n grid, in groups of GM tile rows: inside a
+// group the tile rows run fastest, so the tiles in flight at once (one per
+// SM) cover GM rows of A and a few column blocks of B, which stay in L2.
+constexpr int GM = 16;
+FX_D void tile_of(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int group = t / (GM * tiles_n);
+  const int first = group * GM;
+  const int gsize = tiles_m - first < GM ? tiles_m - first : GM;
+  const int within = t - group * GM * tiles_n;
+  tm = first + within % gsize;
+  tn = within / gsize;
+}
+
+constexpr int CW = 16;   // epilogue columns per TMEM load
+
+// Z (M x N, column-major, ldz) = E(P) with P = op(A) op(B) of K terms, on a
+// persistent grid: CTA b takes tiles b, b + gridDim.x, ... The MMA warp
+// alternates between two TMEM accumulators (columns 0..255 and 256..511),
+// so the epilogue of one tile runs while the next tile is multiplied.
 // AMN / BMN: the A / B tiles are MN-major (else K-major). PS: the slot of
 // the product leaf in E.
 template <class T, bool AMN, bool BMN, class E, int PS>
@@ -172,14 +208,19 @@ __global__ void __launch_bounds__(192, 1)
                                        ~uintptr_t(1023));
   Bars& bars = *reinterpret_cast<Bars*>(smem + NS * STAGE);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  const int ntiles = tiles_m * tiles_n;
   const int nk = (K + BK - 1) / BK;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       tma::mbar_init(&bars.full[s], 1);
       tma::mbar_init(&bars.empty[s], 1);
     }
-    tma::mbar_init(&bars.acc, 1);
+    for (int b = 0; b < 2; ++b) {
+      tma::mbar_init(&bars.accf[b], 1);
+      tma::mbar_init(&bars.acce[b], 4);
+    }
+    tma::mbar_init(&bars.drain, 1);
     bars.abort = 0;
     tma::fence_mbar_init();
   }
@@ -193,102 +234,146 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tbase = bars.taddr;
 
   if (warp == 0) {
-    if (lane == 0) {  // producer
-      int kt = 0;
+    if (lane == 0) {  // producer: every tile's K steps through one ring
+      uint32_t g = 0;
       bool ok = true;
-      for (; kt < nk; ++kt) {
-        const int s = kt % NS;
-        if (kt >= NS && !tma::wait(&bars.empty[s], uint32_t(((kt - NS) / NS) & 1), err)) {
-          ok = false;
-          break;
-        }
-        char* sa = smem + s * STAGE;
-        char* sb = sa + SA;
-        const int k0 = kt * BK;
-        // boxes that start outside the matrix are skipped (their rows or
-        // columns of the product are never stored); partly outside boxes
-        // read zeros there
-        uint32_t bytes = 0;
-        if (AMN) {
-          bytes += uint32_t(m0 < M) * (SA / 2) + uint32_t(m0 + 64 < M) * (SA / 2);
-        } else {
-          bytes += SA;
-        }
-        if (BMN) {
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int tm, tn;
+        tile_of(t, tiles_m, tiles_n, tm, tn);
+        const int m0 = tm * BM, n0 = tn * BN;
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = int(g % NS);
+          if (g >= uint32_t(NS) && !tma::wait(&bars.empty[s], ((g - NS) / NS) & 1u, err)) {
+            ok = false;
+            break;
+          }
+          char* sa = smem + s * STAGE;
+          char* sb = sa + SA;
+          const int k0 = kt * BK;
+          // boxes that start outside the matrix are skipped (their rows or
+          // columns of the product are never stored); partly outside boxes
+          // read zeros there
+          uint32_t bytes = 0;
+          if (AMN) {
+            bytes += uint32_t(m0 < M) * (SA / 2) + uint32_t(m0 + 64 < M) * (SA / 2);
+          } else {
+            bytes += SA;
+          }
+          if (BMN) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) bytes += uint32_t(n0 + 64 * j < N) * (SB / 4);
-        } else {
-          bytes += SB;
-        }
-        tma::arrive_expect_tx(&bars.full[s], bytes);
-        if (AMN) {
-          if (m0 < M) tma::load_2d(sa, &mapA, m0, k0, &bars.full[s]);
-          if (m0 + 64 < M) tma::load_2d(sa + SA / 2, &mapA, m0 + 64, k0, &bars.full[s]);
-        } else {
-          tma::load_2d(sa, &mapA, k0, m0, &bars.full[s]);
-        }
-        if (BMN) {
+            for (int j = 0; j < 4; ++j) bytes += uint32_t(n0 + 64 * j < N) * (SB / 4);
+          } else {
+            bytes += SB;
+          }
+          tma::arrive_expect_tx(&bars.full[s], bytes);
+          if (AMN) {
+            if (m0 < M) tma::load_2d(sa, &mapA, m0, k0, &bars.full[s]);
+            if (m0 + 64 < M) tma::load_2d(sa + SA / 2, &mapA, m0 + 64, k0, &bars.full[s]);
+          } else {
+            tma::load_2d(sa, &mapA, k0, m0, &bars.full[s]);
+          }
+          if (BMN) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (n0 + 64 * j < N) tma::load_2d(sb + j * (SB / 4), &mapB, n0 + 64 * j, k0, &bars.full[s]);
-        } else {
-          tma::load_2d(sb, &mapB, k0, n0, &bars.full[s]);
+            for (int j = 0; j < 4; ++j)
+              if (n0 + 64 * j < N)
+                tma::load_2d(sb + j * (SB / 4), &mapB, n0 + 64 * j, k0, &bars.full[s]);
+          } else {
+            tma::load_2d(sb, &mapB, k0, n0, &bars.full[s]);
+          }
         }
       }
-      if (!ok) {
+      if (!ok) {  // wait (bounded) for the copies still in flight
         bars.abort = 1;
-        for (int j = (kt > NS ? kt - NS : 0); j < kt; ++j)
-          tma::wait(&bars.full[j % NS], uint32_t((j / NS) & 1), nullptr);
+        for (uint32_t j = (g > uint32_t(NS) ? g - NS : 0); j < g; ++j)
+          tma::wait(&bars.full[j % NS], (j / NS) & 1u, nullptr);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       constexpr uint32_t ID = idesc<T, AMN, BMN>();
-      for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt % NS;
-        if (!tma::wait(&bars.full[s], uint32_t((kt / NS) & 1), err)) {
-          bars.abort = 1;
+      uint32_t g = 0;
+      int i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        // the epilogue has read out what this buffer held two tiles ago
+        if (i >= 2 && !tma::wait(&bars.acce[b], uint32_t((i - 2) / 2) & 1u, err)) {
+          ok = false;
           break;
         }
         fence_after();
-        const uint32_t sa = tma::saddr(smem + s * STAGE);
-        const uint32_t sb = sa + SA;
+        const uint32_t tacc = tbase + uint32_t(b * BN);
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = int(g % NS);
+          if (!tma::wait(&bars.full[s], (g / NS) & 1u, err)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = tma::saddr(smem + s * STAGE);
+          const uint32_t sb = sa + SA;
 #pragma unroll
-        for (int k = 0; k < BK / UK; ++k) {
-          const uint64_t ad = AMN ? desc(sa + k * UK * 128, SA / 2, 1024)
-                                  : desc(sa + k * UK * 2, 16, 1024);
-          const uint64_t bd = BMN ? desc(sb + k * UK * 128, SB / 4, 1024)
-                                  : desc(sb + k * UK * 2, 16, 1024);
-          mma(tbase, ad, bd, ID, (kt > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < BK / UK; ++k) {
+            const uint64_t ad = AMN ? desc(sa + k * UK * 128, SA / 2, 1024)
+                                    : desc(sa + k * UK * 2, 16, 1024);
+            const uint64_t bd = BMN ? desc(sb + k * UK * 128, SB / 4, 1024)
+                                    : desc(sb + k * UK * 2, 16, 1024);
+            mma(tacc, ad, bd, ID, (kt > 0 || k > 0) ? 1u : 0u);
+          }
+          commit(&bars.empty[s]);
         }
-        commit(&bars.empty[s]);
+        if (ok) commit(&bars.accf[b]);
       }
-      commit(&bars.acc);
+      if (!ok) {  // wake the epilogue (it sees the abort) after what was issued
+        bars.abort = 1;
+        commit(&bars.accf[0]);
+        commit(&bars.accf[1]);
+      }
+      commit(&bars.drain);
+      tma::wait(&bars.drain, 0u, err);
     }
     __syncwarp();
   } else {  // epilogue: warps 2..5 take TMEM lane quarters 2, 3, 0, 1
     const int q = warp & 3;
-    const bool ready = tma::wait(&bars.acc, 0u, err);
-    fence_after();
-    const int64_t m = int64_t(m0) + q * 32 + lane;
-    // the TMEM loads below are warp-wide: the warp decides together
-    const bool go = __all_sync(0xffffffffu, ready && !bars.abort);
-    if (go) {
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1;
+      const bool ready = tma::wait(&bars.accf[b], uint32_t(i / 2) & 1u, err);
+      fence_after();
+      // the TMEM loads below are warp-wide: the warp decides together
+      if (!__all_sync(0xffffffffu, ready && !bars.abort)) break;
+      int tm, tn;
+      tile_of(t, tiles_m, tiles_n, tm, tn);
+      const int64_t m = int64_t(tm) * BM + q * 32 + lane;
+      const int n0 = tn * BN;
+      const bool row = m < M;
+      T wn[NL][CW], wc[NL][CW];
+      if (row) load_others<LL, PS, T, CW>(wn, sl, m, n0, N - n0 < CW ? N - n0 : CW);
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        const int nc = n0 + c * 32;
-        uint32_t r[32];
-        ld32(tbase + (uint32_t(q * 32) << 16) + uint32_t(c * 32), r);
+      for (int c = 0; c < BN / CW; ++c) {
+        const int nc = n0 + c * CW;
+        uint32_t r[CW];
+        ld16(tbase + uint32_t(b * BN) + (uint32_t(q * 32) << 16) + uint32_t(c * CW), r);
         wait_ld();
+        if (c == BN / CW - 1) {  // the accumulator buffer is free for the MMA warp
+          fence_before();
+          __syncwarp();
+          if (lane == 0) tma::arrive(&bars.acce[b]);
+        }
         if (nc >= N) continue;  // warp-uniform
-        const int nn = N - nc < 32 ? N - nc : 32;
-        if (m < M) {
-          float vals[NL][32];
-          load_others<LL, PS>(vals, sl, m, nc, nn);
+        const int nn = N - nc < CW ? N - nc : CW;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+          for (int j = 0; j < CW; ++j) wc[l][j] = wn[l][j];
+        const int nx = nc + CW;
+        if (row && c + 1 < BN / CW && nx < N)
+          load_others<LL, PS, T, CW>(wn, sl, m, nx, N - nx < CW ? N - nx : CW);
+        if (row) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
             if (j < nn) {
-              ECtx<LL, PS> cx{vals, __uint_as_float(r[j]), j};
+              ECtx<LL, PS, T, CW> cx{wc, __uint_as_float(r[j]), j};
               sstore(z + m + int64_t(nc + j) * ldz, narrow_to<T>::from(e.ev(cx)));
             }
           }
