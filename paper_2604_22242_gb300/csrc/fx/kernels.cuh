@@ -756,11 +756,12 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
     acc.init();
     max_acc_t<E, CT> mx;
     mx.init();
-    CT facc[FMA64 ? U : 1][FMA64 ? V : 1];
+    // one accumulator per lane, the U vectors of a step folded in order: an
+    // FP64 fma holds the FP64 unit for many cycles per warp anyway, and
+    // fewer live registers keep two blocks resident per SM
+    CT facc[FMA64 ? V : 1];
 #pragma unroll
-    for (int u = 0; u < (FMA64 ? U : 1); ++u)
-#pragma unroll
-      for (int j = 0; j < (FMA64 ? V : 1); ++j) facc[u][j] = CT(0);
+    for (int j = 0; j < (FMA64 ? V : 1); ++j) facc[j] = CT(0);
     if (c < C) {
       for (int64_t rb = int64_t(lane) * V; rb < R; rb += int64_t(G) * V * U) {
         Pack<LL, V, CT> p[U];
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
               if (j < nv) {
                 CT x, y;
                 term_parts<false>(e, p[u], j, x, y);
-                facc[u][j] = __fma_rn(x, y, facc[u][j]);
+                facc[j] = __fma_rn(x, y, facc[j]);
               }
             }
           }
@@ -813,14 +814,7 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
         if (!ISMAX) acc.add(lane_sum(vs));
       }
     }
-    if constexpr (FMA64) {
-      CT w[U * V];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int j = 0; j < V; ++j) w[u * V + j] = facc[u][j];
-      acc.add(lane_sum(w));
-    }
+    if constexpr (FMA64) acc.add(lane_sum(facc));
     const CT m = mx.get();
     CT res;
     if constexpr (G == 32) {

@@ -24,10 +24,19 @@ struct Run {
   int* launches;
   cudaStream_t st;
   Workspace* errws;  // error word of the bulk kernels' bounded waits
+  Workspace* tick;   // completion tickets (zero between launches)
 };
 
 inline Run run_of(fx_expr* x, cudaStream_t st) {
-  return Run{x->b, x->e->n_in, x->tune, &x->ws, &x->last_launches, st, &x->ws_err};
+  return Run{x->b, x->e->n_in, x->tune, &x->ws, &x->last_launches, st, &x->ws_err, &x->ws_tick};
+}
+
+// n completion tickets, zero on entry (fresh workspace is zeroed; every
+// launch's last block resets what it used).
+inline fx_status tickets(const Run& r, int64_t n, unsigned int** out) {
+  FX_TRY(r.tick->ensure(size_t(n > 0 ? n : 1) * sizeof(unsigned int), r.st));
+  *out = static_cast<unsigned int*>(r.tick->p);
+  return FX_OK;
 }
 
 inline fx_status err_word(const Run& r, unsigned int** out) {
@@ -215,13 +224,12 @@ inline fx_status after_launch(const Run& r, const char* what) {
   return FX_OK;
 }
 
-// Reduction workspace for `grid` partials plus one ticket.
+// Reduction workspace for `grid` partials, and the completion ticket.
 inline fx_status red_space(const Run& r, int grid, RedArgs& red) {
   const size_t part = size_t(grid) * sizeof(double2);
   FX_TRY(r.ws->ensure(part + 256, r.st));
   red.part = static_cast<double2*>(r.ws->p);
-  red.ticket = reinterpret_cast<unsigned int*>(static_cast<char*>(r.ws->p) + part);
-  return FX_OK;
+  return tickets(r, 1, &red.ticket);
 }
 
 template <class E, class Epi, int V, int U>
@@ -623,12 +631,11 @@ fx_status launch_row(const Run& r, const E& e, const Slots& sl, int64_t R, int64
     if (S > 1) {
       const size_t part = size_t(S) * R * sizeof(double2);
       const size_t partm = size_t(S) * R * sizeof(CT);
-      const size_t tick = size_t(gx) * sizeof(unsigned int);
-      FX_TRY(r.ws->ensure(part + partm + tick + 512, r.st));
+      FX_TRY(r.ws->ensure(part + partm + 512, r.st));
       char* w = static_cast<char*>(r.ws->p);
       rr.part = reinterpret_cast<double2*>(w);
       rr.partm = w + part;
-      rr.tickets = reinterpret_cast<unsigned int*>(w + ((part + partm + 255) & ~size_t(255)));
+      FX_TRY(tickets(r, gx, &rr.tickets));
     }
     return FX_OK;
   };
@@ -740,9 +747,9 @@ fx_status run_backward(fx_expr* x, const Root& root, const void* gout, void* con
       ga.S = int(S);
       if (NBC > 0) {
         const size_t part = size_t(NBC) * S * R * sizeof(double2);
-        FX_TRY(x->ws.ensure(part + size_t(gx) * 4 + 512, st));
+        FX_TRY(x->ws.ensure(part + 512, st));
         ga.part = static_cast<double2*>(x->ws.p);
-        ga.tickets = reinterpret_cast<unsigned int*>(static_cast<char*>(x->ws.p) + ((part + 255) & ~size_t(255)));
+        FX_TRY(tickets(r, gx, &ga.tickets));
       }
       return FX_OK;
     };

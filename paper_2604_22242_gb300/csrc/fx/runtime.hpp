@@ -56,6 +56,11 @@ struct fx_expr {
   fx::Workspace ws_tmp;  // unfused intermediates
   fx::Workspace ws_err;  // error word of bounded waits (kErrTimeout)
   fx::Workspace ws_gemm; // matrix products of a tree (fusion boundaries)
+  // completion tickets of the cross-block combines, apart from the partial
+  // sums: launches with different grids (tuning, the unfused baseline) lay
+  // their partials out differently, and a ticket inside that area would be
+  // overwritten; every launch's last block resets the tickets it used
+  fx::Workspace ws_tick;
   fx::Tune tune;
   int last_launches = 0;
   fx::BatchCache* batch = nullptr;

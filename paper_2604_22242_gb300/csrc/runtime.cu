@@ -220,6 +220,7 @@ fx_status fx_expr_destroy(fx_expr* x) {
   x->ws_tmp.release();
   x->ws_err.release();
   x->ws_gemm.release();
+  x->ws_tick.release();
   delete x;
   return FX_OK;
 }
@@ -551,6 +552,9 @@ fx_status fx_expr_sync_status(fx_expr* x, void* stream) {
   FX_CUDA(cudaMemcpy(&word, x->ws_err.p, sizeof word, cudaMemcpyDeviceToHost));
   if (word == 0) return FX_OK;
   FX_CUDA(cudaMemset(x->ws_err.p, 0, sizeof word));
+  // a block that gave up skipped its combine and left its ticket counted:
+  // start the next evaluation from cleared tickets
+  if (x->ws_tick.p) FX_CUDA(cudaMemset(x->ws_tick.p, 0, x->ws_tick.bytes));
   return fail(FX_E_CUDA, "a kernel of '%s' gave up a bounded wait for its bulk copies (code %u)",
               x->e->name, word);
 }

@@ -275,3 +275,67 @@ def test_workload_16384_clamped(fx, env16384):
     env2 = dict(env, C=clamped)
     rep = full_check(fx, "schur_exp_trans_sqdiff", storage, env2, R, C, " at 16384^2, C <= 9")["Z"]
     assert rep.overflow == 0
+
+
+@pytest.mark.parametrize("name", ["sqdiff_accu", "diff_norm", "absdiff_rowmax", "schur_colsum",
+                                  "schur_trans_accu", "schur_exp_trans_sqdiff", "sigmoid_sqloss"])
+def test_alternating_evaluations_on_one_object(fx, name):
+    """One expression object evaluated fused, unfused and fused again under
+    launch shapes with different grids (so the partial sums are laid out
+    differently each time): every result is complete and correct. The
+    combines' completion tickets live apart from the partials."""
+    import torch
+    from harness import STORAGE_CODE, canary_buffer, from_device, to_device
+    R, C = 1000, 700
+    env = env_for(name, "f32", R, C, seed=77)
+    ref = oracle_outputs(name, env)
+    h = fx.fx_expr_create(name, STORAGE_CODE["f32"])
+    try:
+        n_in, n_out, _, kind = fx.fx_expr_info(h)
+        keep = []
+        for k, s in enumerate(SLOTS[name]):
+            b = env[s]
+            t = to_device(b)
+            keep.append(t)
+            fx.fx_expr_bind(h, k, t.data_ptr(), b.rows, b.cols, b.ld)
+        outs = {}
+        if kind in ("elementwise", "multi"):
+            z = canary_buffer(R * C, torch.float32)
+            fx.fx_expr_bind(h, n_in, z.data_ptr(), R, C, R)
+            outs["Z"] = z
+        if kind in ("full_reduce", "multi"):
+            s = canary_buffer(1, torch.float32)
+            fx.fx_expr_bind(h, n_in + (1 if kind == "multi" else 0), s.data_ptr(), 1, 1, 1)
+            outs["s"] = s
+        if kind == "dim_reduce":
+            nv = C if name == "schur_colsum" else R
+            v = canary_buffer(nv, torch.float32)
+            if name == "schur_colsum":
+                fx.fx_expr_bind(h, n_in, v.data_ptr(), 1, C, 1)
+            else:
+                fx.fx_expr_bind(h, n_in, v.data_ptr(), R, 1, R)
+            outs["v"] = v
+        steps = [("fused", (256, 4, 0, 0)), ("unfused", None), ("fused", (256, 4, 0, 0)),
+                 ("fused", (64, 2, 1, 2)), ("fused", (512, 8, 0, 1)), ("unfused", None),
+                 ("fused", (128, 2, 2, 0))]
+        for i, (how, shape) in enumerate(steps):
+            for t in outs.values():
+                t.fill_(float("nan"))
+            if shape:
+                fx.fx_expr_set_launch_shape(h, *shape)
+                fx.fx_eval(h, 0)
+            else:
+                fx.fx_eval_unfused(h, 0)
+            torch.cuda.synchronize()
+            fx.fx_expr_sync_status(h, 0)
+            got = {}
+            for key, t in outs.items():
+                if key == "Z":
+                    got["Z"] = from_device(t[:R * C], "f32").reshape(C, R).T
+                elif key == "s":
+                    got["s"] = from_device(t[:1], "f64")[0]
+                else:
+                    got["v"] = from_device(t[:len(t) - 64], "f64")
+            check(name, "f32", got, ref, f" step {i} ({how}, {shape})")
+    finally:
+        fx.fx_expr_destroy(h)
