@@ -442,6 +442,7 @@ __global__ void __launch_bounds__(NTC + 32) k_bwd_bulk(const E e, const Slots sl
     const int64_t c0 = cb + k * CPS;
     const int nc = int(ce - c0 < CPS ? ce - c0 : CPS);
     if (nvalid > 0) {
+      CT bpart[NB][V] = {};  // this stage's columns, summed plainly
       for (int jc = 0; jc < nc; ++jc) {
         Pack<LL, V, CT> p;
         load_stage<LL, V, CT, TRB>(p, hold, smem + (st * CPS + jc) * SBC, sl, t, c0 + jc, nvalid);
@@ -453,7 +454,13 @@ __global__ void __launch_bounds__(NTC + 32) k_bwd_bulk(const E e, const Slots sl
           Ctx<LL, V, CT> cx{p, j};
           e.bwd(cx, gL, g[j]);
         }
-        bwd_store<LL, V, CT, NB>(g, bacc, ga, r, c0 + jc, R, nvalid);
+        bwd_store<LL, V, CT, NB>(g, bpart, ga, r, c0 + jc, R, nvalid);
+      }
+      if constexpr (NBC > 0) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int j = 0; j < V; ++j) bacc[b][j].add(bpart[b][j]);
       }
     }
     tma::arrive(&ring.empty[st]);

@@ -1022,9 +1022,11 @@ template <class LL, int I, int J = 0> FX_HD constexpr int bc_rank() {
 }
 
 // Writes the plain leaves' gradients at (r.., c) and adds the each_col
-// leaves' partial derivatives to their per-row running sums.
+// leaves' partial derivatives to per-row plain partial sums (the caller
+// folds those into the compensated running sums once per group of
+// columns: one compensated add per group instead of per element).
 template <class LL, int V, class CT, int NB, int I = 0>
-FX_D void bwd_store(const GradAcc<LL, CT> (&g)[V], ThreadSum<CT> (&bacc)[NB][V],
+FX_D void bwd_store(const GradAcc<LL, CT> (&g)[V], CT (&bpart)[NB][V],
                     const GradArgs& ga, int64_t r, int64_t c, int64_t R, int nvalid) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
@@ -1048,9 +1050,9 @@ FX_D void bwd_store(const GradAcc<LL, CT> (&g)[V], ThreadSum<CT> (&bacc)[NB][V],
       constexpr int b = bc_rank<LL, I>();
 #pragma unroll
       for (int j = 0; j < V; ++j)
-        if (j < nvalid) bacc[b][j].add(g[j].g[I]);
+        if (j < nvalid) bpart[b][j] += g[j].g[I];
     }
-    bwd_store<LL, V, CT, NB, I + 1>(g, bacc, ga, r, c, R, nvalid);
+    bwd_store<LL, V, CT, NB, I + 1>(g, bpart, ga, r, c, R, nvalid);
   }
 }
 
@@ -1136,6 +1138,7 @@ __global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (c + u < ce) load_rc(p[u], sl, r, c + u, nvalid);
+      CT bpart[NBC > 0 ? NBC : 1][V] = {};
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (c + u < ce) {
@@ -1147,8 +1150,14 @@ __global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int
             Ctx<LL, V, CT> cx{p[u], j};
             e.bwd(cx, gL, g[j]);
           }
-          bwd_store<LL, V, CT, (NBC > 0 ? NBC : 1)>(g, bacc, ga, r, c + u, R, nvalid);
+          bwd_store<LL, V, CT, (NBC > 0 ? NBC : 1)>(g, bpart, ga, r, c + u, R, nvalid);
         }
+      }
+      if constexpr (NBC > 0) {
+#pragma unroll
+        for (int b = 0; b < NBC; ++b)
+#pragma unroll
+          for (int j = 0; j < V; ++j) bacc[b][j].add(bpart[b][j]);
       }
     }
   }
