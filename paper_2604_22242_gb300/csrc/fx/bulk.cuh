@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(NTC + 32) k_row_bulk(const E e, const Slots sl
         Pack<LL, V, CT> p;
         load_stage<LL, V, CT, TRB>(p, hold, smem + (st * CPS + j) * SBC, sl, t, c0 + j, nvalid);
         CT v[V];
-        eval_lanes<V>(e, p, v);
+        eval_lanes<V>(max_tree<ISMAX, CT>(e), p, v);
 #pragma unroll
         for (int q = 0; q < V; ++q) {
           if (ISMAX) mx[q].add(v[q]);
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(NTC + 32) k_bwd_bulk(const E e, const Slots sl
 #pragma unroll
         for (int j = 0; j < V; ++j) {
 #pragma unroll
-          for (int q = 0; q < NL; ++q) g[j].g[q] = CT(0);
+          for (int q = 0; q < NL; ++q) g[j].g[q] = grad_zero<CT>();
           Ctx<LL, V, CT> cx{p, j};
           e.bwd(cx, gL, g[j]);
         }

@@ -363,14 +363,23 @@ template <class CT, bool INT> struct MaxAcc {
 template <> struct MaxAcc<double, true> {
   long long m;
   FX_D void init() { m = -1; }
+  // v is the abs node's operand: its magnitude is the pattern with the sign
+  // bit cleared (an integer and, not an FP64 instruction)
   FX_D void add(double v) {
-    const long long b = __double_as_longlong(v);
+    const long long b = __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll;
     m = b > m ? b : m;
   }
   FX_D double get() const { return m < 0 ? neg_inf<double>() : __longlong_as_double(m); }
 };
 template <class E, class CT>
 using max_acc_t = MaxAcc<CT, std::is_same<CT, double>::value && abs_root<E>::value>;
+
+// The tree whose values a maximum takes: for an FP64 maximum of magnitudes
+// the abs node's operand (MaxAcc clears the sign bit itself), else the tree.
+template <bool ISMAX, class CT, class E> FX_D const auto& max_tree(const E& e) {
+  if constexpr (ISMAX && std::is_same<CT, double>::value && abs_root<E>::value) return e.e;
+  else return e;
+}
 
 // ---------------------------------------------------------------- combines
 
@@ -797,7 +806,7 @@ __global__ void __launch_bounds__(NT) k_col(const E e, const Slots sl, const int
           vs[u] = CT(0);
           if (nv > 0) {
             CT v[V];
-            eval_lanes<V>(e, p[u], v);
+            eval_lanes<V>(max_tree<ISMAX, CT>(e), p[u], v);
             if (ISMAX) {
 #pragma unroll
               for (int j = 0; j < V; ++j)
@@ -969,7 +978,7 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
       for (int u = 0; u < U; ++u) {
         if (c + u < ce) {
           CT v[V];
-          eval_lanes<V>(e, p[u], v);
+          eval_lanes<V>(max_tree<ISMAX, CT>(e), p[u], v);
 #pragma unroll
           for (int j = 0; j < V; ++j) {
             if (ISMAX) mx[j].add(v[j]);
@@ -992,6 +1001,10 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
 // local partial derivative. Plain leaves get dL/dleaf written element by
 // element; each_col leaves (vectors indexed by row) get their row sums,
 // accumulated per thread and combined across column splits like k_row.
+
+// The adjoints start at -0: -0 + a == a exactly for every a (+0 + a is not,
+// for a = -0), so the compiler may drop the first add into each adjoint.
+template <class CT> FX_D CT grad_zero() { return -CT(0); }
 
 template <class LL, class CT> struct GradAcc {
   CT g[tl_size<LL>::value];
@@ -1146,7 +1159,7 @@ __global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int
 #pragma unroll
           for (int j = 0; j < V; ++j) {
 #pragma unroll
-            for (int k = 0; k < NL; ++k) g[j].g[k] = CT(0);
+            for (int k = 0; k < NL; ++k) g[j].g[k] = grad_zero<CT>();
             Ctx<LL, V, CT> cx{p[u], j};
             e.bwd(cx, gL, g[j]);
           }

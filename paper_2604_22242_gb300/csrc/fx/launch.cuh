@@ -605,7 +605,11 @@ template <class E, bool ISMAX, int V>
 fx_status launch_col(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C, void* out,
                      int64_t ldo) {
   constexpr int NT = 256, U = tl_size<leaves_t<E>>::value <= 2 ? 8 : 4;
-  if (R >= 1024) {
+  // a block per column for long FP32 columns; a warp per column otherwise,
+  // and for FP64 up to 2^16 rows: its slow FP64 unit leaves a block per
+  // column waiting on the block-wide merge after only a few steps
+  constexpr bool dbl = std::is_same<ct_of<E>, double>::value;
+  if (R >= (dbl ? 65536 : 1024)) {
     auto kern = k_col<E, ISMAX, V, U, NT, NT>;
     const int grid = grid_for(kern, NT, C > 0 ? C : 1, r.tune);
     kern<<<grid, NT, 0, r.st>>>(e, sl, R, C, out, ldo);
