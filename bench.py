@@ -69,12 +69,12 @@ TRAFFIC = {
     # timed launch of Z at 8192^2 FP32 (profiles/k_flat_schur_sqrt_sigmoid_f32.md),
     # per (threads per block, vectors per leaf) of the register kernel k_flat
     # (pipelines 0 and 2 of this four-leaf tree; the blocks-per-SM cap only
-    # changes the grid of the same streaming loop). Unroll 2: 1,073,772,800
-    # read + 241,834,496 written; unroll 4: 1,073,857,024 + 241,025,024 (the
+    # changes the grid of the same streaming loop). Unroll 2: 1,073,888,000
+    # read + 241,666,816 written; unroll 4: 1,073,778,432 + 241,022,976 (the
     # rest of Z still in L2 when the launch ends).
-    ("expr8192", "Z"): {"hash": "ea360771f9e42b1e",
-                        "bytes": {(256, 2): 1073772800 + 241834496,
-                                  (256, 4): 1073857024 + 241025024}},
+    ("expr8192", "Z"): {"hash": "dfc4e90a34ae43b9",
+                        "bytes": {(256, 2): 1073888000 + 241666816,
+                                  (256, 4): 1073778432 + 241022976}},
 }
 
 # FP64-pipe instructions per output element of FP64 trees (per lane: DFMA,
