@@ -602,7 +602,24 @@ ORACLE_OF = {
     "schur_exp_trans_sqdiff": ("(- (+ (% A B) (* 3.5 (exp C))) (t D))", "(accu (square (- A B)))"),
     "schur_trans_accu": "(+ (% A B) (* 0.5 (t C)))",
     "sigmoid_sqloss": "(accu (square (- (sigmoid (+ (% X W) (each_col b))) Y)))",
+    # the Sec. 4 suite, with the scalars the library's definitions default to
+    "expr1": "(+ (* 2.0 (+ (t X) Y)) (* 2.0 (+ X (t Y))))",
+    "expr2": "(+ (+ (* 0.75 A) (t (+ B C))) (log (pow D 2.0)))",
+    "expr3": "(/ 1 (+ (% X (f32 Y)) (log (% (log (+ X 2)) W))))",
+    "relu": "(% X (gt X 0.0))",
+    "sigmoid": "(/ 1.0 (+ 1.0 (exp (neg X))))",
+    "swish": "(/ X (+ 1 (exp (neg (* 1.0 X)))))",
+    "gelu": "(% (/ X 2) (+ 1 (tanh (* 0.7978845608028654 (+ X (* 0.044715 (pow X 3)))))))",
 }
+# slot names of the oracle trees, in slot order, where they differ from the
+# names of the workload's operands bound to them
+ORACLE_SLOTS = {"expr1": ["X", "Y"], "expr2": ["A", "B", "C", "D"], "expr3": ["X", "Y", "W"],
+                "relu": ["X"], "sigmoid": ["X"], "swish": ["X"], "gelu": ["X"]}
+for _n in range(2, 17):
+    _t = "A1"
+    for _k in range(2, _n + 1):
+        _t = f"(+ {_t} A{_k})"
+    ORACLE_OF[f"add{_n}"] = _t
 
 
 def _host64(t):
@@ -628,14 +645,17 @@ def oracle_errors(keep, storage, n_sample=1 << 16):
     for name, key, ins, kind in keep.get("trees", []):
         tree = ORACLE_OF[name]
         _, o = keep[key]
+        tenv = env
+        if name in ORACLE_SLOTS:
+            tenv = {slot: env[i] for slot, i in zip(ORACLE_SLOTS[name], ins)}
         if kind == "Zs":     # Z of the first tree, s = accu of the second
             tree, side = tree
             o, osum = o
             g = _host64(osum).ravel()
 
-            def sjob(side=side, g=g):
-                v, sg = oracle.evaluate_sigma(side, env)
-                m = oracle.evaluate_mag(side, env)
+            def sjob(side=side, g=g, tenv=tenv):
+                v, sg = oracle.evaluate_sigma(side, tenv)
+                m = oracle.evaluate_mag(side, tenv)
                 return ErrorReport(rst, tolerance(side, storage), gate_scale(side)).add(
                     g, v.ravel(), sg.ravel(), m.ravel())
             jobs["s"] = sjob
@@ -648,18 +668,18 @@ def oracle_errors(keep, storage, n_sample=1 << 16):
             cc = rng.integers(0, C, n_sample)
             g = _host64(o[torch.from_numpy(rr + cc * R).to(o.device)])
 
-            def zjob(tree=tree, rr=rr, cc=cc, g=g):
-                v, sg = oracle.at_sigma(tree, env, rr, cc)
-                m = oracle.at_mag(tree, env, rr, cc)
+            def zjob(tree=tree, rr=rr, cc=cc, g=g, tenv=tenv):
+                v, sg = oracle.at_sigma(tree, tenv, rr, cc)
+                m = oracle.at_mag(tree, tenv, rr, cc)
                 return ErrorReport(storage, tolerance(tree, storage), gate_scale(tree)).add(
                     g, v, sg, m)
             jobs[key] = zjob
         else:
             g = _host64(o).ravel()
 
-            def rjob(tree=tree, g=g):
-                v, sg = oracle.evaluate_sigma(tree, env)
-                m = oracle.evaluate_mag(tree, env)
+            def rjob(tree=tree, g=g, tenv=tenv):
+                v, sg = oracle.evaluate_sigma(tree, tenv)
+                m = oracle.evaluate_mag(tree, tenv)
                 return ErrorReport(rst, tolerance(tree, storage), gate_scale(tree)).add(
                     g, v.ravel(), sg.ravel(), m.ravel())
             jobs[key] = rjob

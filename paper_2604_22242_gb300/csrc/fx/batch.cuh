@@ -93,8 +93,11 @@ template <int NIN> struct IssueDesc {
 };
 
 // Row shift of tile column c: its rows are r0 - shift .. r0 - shift + TR - 1.
+// W is a power of two, so the residue needs only the low 32 bits of the
+// product and the sum.
 template <int W> FX_D int col_skew(int64_t sld, int sbase, int64_t col) {
-  return sld > 0 ? int((uint64_t(sbase) + uint64_t(col) * uint64_t(sld)) % uint64_t(W)) : 0;
+  static_assert((W & (W - 1)) == 0, "skew width is a power of two");
+  return sld > 0 ? int((uint32_t(sbase) + uint32_t(col) * uint32_t(sld)) & uint32_t(W - 1)) : 0;
 }
 
 template <int NIN, int TR, int TC, int KIND, int KW>
@@ -145,18 +148,21 @@ FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d) {
     const int ld = int(d.ld[L::slot]);
     const int rr = int(d.R - d.r0), cc = int(d.C - d.c0);  // rows / cols left in the matrix
     if constexpr (L::mode == MN) {
-      // column c holds rows r0 - s_c .. r0 - s_c + TR - 1 (s_c its skew)
+      // column c holds rows r0 - s_c .. r0 - s_c + TR - 1 (s_c its skew);
+      // offsets from the tile's first column are 32-bit
       const T* src = static_cast<const T*>(d.p[L::slot]) + d.c0 * int64_t(ld);
       constexpr int W = 16 / int(sizeof(T));
       constexpr int CPC = TR / W;  // chunks per column
       static_assert(NT % CPC == 0 && TC % (NT / CPC) == 0, "chunk copy shape");
       const int q = (threadIdx.x % CPC) * W;
       const int R = int(d.R);
+      const int r0 = int(d.r0);
+      const uint32_t c0 = uint32_t(d.c0);
 #pragma unroll
       for (int c = threadIdx.x / CPC; c < TC; c += NT / CPC) {
         if (c >= cc) break;
-        const int row = int(d.r0) - col_skew<W>(d.sld, d.sbase, d.c0 + c) + q;
-        const T* s = src + row + c * ld;
+        const int row = r0 - col_skew<W>(d.sld, d.sbase, c0 + c) + q;
+        const T* s = src + (row + c * ld);
         T* t = dst + c * TR + q;
         if (row >= 0 && row + W <= R && (reinterpret_cast<uintptr_t>(s) & 15) == 0) {
           cpa::copy16(t, s);
@@ -168,17 +174,27 @@ FX_D void issue_tile(char* buf, const IssueDesc<NIN>& d) {
       }
     } else if constexpr (L::mode == MT) {
       // output rows r0 - (W - 1) .. r0 + TR - 1: stored row k is output row
-      // r0 - (W - 1) + k, i.e. D's column of that index
+      // r0 - (W - 1) + k, i.e. D's column of that index. The stored rows
+      // inside the matrix are kb .. ke - 1; each thread walks its share of
+      // them with pointer steps.
       constexpr int W = 16 / int(sizeof(T));
+      constexpr int KS = NT / TC;  // stored rows per pass of the block
       static_assert(NT % TC == 0, "transposed copy shape");
-      const int64_t rlo = d.r0 - (W - 1);
-      const T* src = static_cast<const T*>(d.p[L::slot]) + d.c0 + rlo * int64_t(ld);
+      const int rlo = int(d.r0) - (W - 1);
+      const int kb = rlo < 0 ? -rlo : 0;
+      const int left = int(d.R) - rlo;
+      const int ke = left < TR + W - 1 ? left : TR + W - 1;
       const int c = threadIdx.x % TC;  // D element (c0 + c, rlo + k)
       if (c < cc) {
-        for (int k = threadIdx.x / TC; k < TR + W - 1; k += NT / TC) {
-          const int64_t row = rlo + k;
-          if (row >= 0 && row < d.R)
-            cpa::copy<int(sizeof(T))>(dst + k * (TC + 1) + c, src + c + int64_t(k) * ld);
+        int k = threadIdx.x / TC;
+        if (k < kb) k += ((kb - k + KS - 1) / KS) * KS;
+        const T* s = static_cast<const T*>(d.p[L::slot]) + d.c0 + c + int64_t(rlo + k) * ld;
+        T* t = dst + k * (TC + 1) + c;
+        const int64_t step = int64_t(KS) * ld;
+        for (; k < ke; k += KS) {
+          cpa::copy<int(sizeof(T))>(t, s);
+          s += step;
+          t += KS * (TC + 1);
         }
       }
     }
@@ -277,38 +293,53 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
     const int i = (threadIdx.x % RG) * V;
     const int cc = int(d.C - d.c0);
     const int R = int(d.R);
-    T* z = KIND != FX_KIND_FULL_REDUCE ? static_cast<T*>(const_cast<void*>(d.z)) : nullptr;
+    const int r0 = int(d.r0);
+    const uint32_t c0 = uint32_t(d.c0);
     const int ldz = int(d.ldz);
+    // Z from the tile's first column on; offsets inside a matrix are 32-bit
+    T* z = KIND != FX_KIND_FULL_REDUCE
+               ? static_cast<T*>(const_cast<void*>(d.z)) + d.c0 * int64_t(ldz)
+               : nullptr;
 #pragma unroll
     for (int c = threadIdx.x / RG; c < TC; c += NT / RG) {
       if (c < cc) {
-        const int sk = col_skew<V>(d.sld, d.sbase, d.c0 + c);
-        const int row = int(d.r0) - sk + i;  // output row of slot i
-        bool ok[V];
-        bool all = true, any = false;
+        const int sk = col_skew<V>(d.sld, d.sbase, c0 + c);
+        const int row = r0 - sk + i;  // output row of slot i
+        Pack<LL, V, CT> p;
+        CT v[V];
+        if (row >= 0 && row + V <= R) {  // all V slots inside the matrix
+          bool all[V];
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-          ok[j] = row + j >= 0 && row + j < R;
-          all = all && ok[j];
-          any = any || ok[j];
-        }
-        if (any) {
-          Pack<LL, V, CT> p;
-          load_tile_vec<LL, V, CT, TR, TC>(p, buf, m, d.r0, d.c0, i, c, sk, ok);
-          CT v[V];
+          for (int j = 0; j < V; ++j) all[j] = true;
+          load_tile_vec<LL, V, CT, TR, TC>(p, buf, m, d.r0, d.c0, i, c, sk, all);
           eval_lanes<V>(e, p, v);
           if constexpr (KIND != FX_KIND_FULL_REDUCE) {
-            T* q = z + row + (d.c0 + c) * int64_t(ldz);
-            if (all && (reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+            T* q = z + (row + c * ldz);
+            if ((reinterpret_cast<uintptr_t>(q) & 15) == 0) {
               Raw<T, V> o;
 #pragma unroll
               for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(v[j]);
               vstore(q, o);
             } else {
 #pragma unroll
-              for (int j = 0; j < V; ++j)
-                if (ok[j]) sstore(q + j, narrow_to<T>::from(v[j]));
+              for (int j = 0; j < V; ++j) sstore(q + j, narrow_to<T>::from(v[j]));
             }
+          }
+          if constexpr (KIND != FX_KIND_ELEMENTWISE) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) tsum += v[j];
+          }
+        } else if (row + V > 0 && row < R) {  // some slots inside
+          bool ok[V];
+#pragma unroll
+          for (int j = 0; j < V; ++j) ok[j] = row + j >= 0 && row + j < R;
+          load_tile_vec<LL, V, CT, TR, TC>(p, buf, m, d.r0, d.c0, i, c, sk, ok);
+          eval_lanes<V>(e, p, v);
+          if constexpr (KIND != FX_KIND_FULL_REDUCE) {
+            T* q = z + (row + c * ldz);
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+              if (ok[j]) sstore(q + j, narrow_to<T>::from(v[j]));
           }
           if constexpr (KIND != FX_KIND_ELEMENTWISE) {
 #pragma unroll
@@ -477,7 +508,7 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
   using CT = ct_of<E>;
   constexpr int V = vec_width<E, 16>();
   constexpr bool dbl = std::is_same<CT, double>::value;
-  constexpr int TR = dbl ? 32 : 64, TCc = 32;
+  constexpr int TR = dbl ? 32 : 64, TCc = 64;
   constexpr int NTMAX = 512;  // partials are sized for the largest block
   const int n_in = NIN;
   if constexpr (root_of<Root>::kind == FX_KIND_DIM_REDUCE) {

@@ -116,7 +116,8 @@ template <class LL, int I = 0> FX_HD constexpr int column_tx_bytes_per_row() {
 
 // Consumer: the thread's V rows of column c, plain leaves from the stage,
 // vectors from `hold` (loaded once per block), each_row scalars from global.
-template <class LL, int V, class CT, int TRB, int I = 0>
+// FULL: the caller knows that all V rows are inside the matrix.
+template <class LL, int V, class CT, int TRB, bool FULL = false, int I = 0>
 FX_D void load_stage(Pack<LL, V, CT>& p, const Pack<LL, V, CT>& hold, const char* stage,
                      const Slots& sl, int t, int64_t c, int nvalid) {
   if constexpr (I < tl_size<LL>::value) {
@@ -125,7 +126,7 @@ FX_D void load_stage(Pack<LL, V, CT>& p, const Pack<LL, V, CT>& hold, const char
     auto& dst = pget<I>::of(p);
     if constexpr (L::mode == MN) {
       const T* q = reinterpret_cast<const T*>(stage + stage_offset<LL, TRB, I>()) + t * V;
-      if (nvalid == V) {
+      if (FULL || nvalid == V) {
         dst = *reinterpret_cast<const Raw<T, V>*>(q);
       } else {
 #pragma unroll
@@ -137,7 +138,7 @@ FX_D void load_stage(Pack<LL, V, CT>& p, const Pack<LL, V, CT>& hold, const char
       const SlotView& s = sl.s[L::slot];
       dst.v[0] = sload(static_cast<const T*>(s.p) + c * s.vs);
     }
-    load_stage<LL, V, CT, TRB, I + 1>(p, hold, stage, sl, t, c, nvalid);
+    load_stage<LL, V, CT, TRB, FULL, I + 1>(p, hold, stage, sl, t, c, nvalid);
   }
 }
 
@@ -395,7 +396,6 @@ __global__ void __launch_bounds__(NTC + 32) k_bwd_bulk(const E e, const Slots sl
                                                         unsigned int* err) {
   using LL = leaves_t<E>;
   using CT = ct_of<E>;
-  constexpr int NL = tl_size<LL>::value;
   constexpr int NBC = count_mode<LL>(MBC);
   constexpr int NB = NBC > 0 ? NBC : 1;
   static_assert(count_mode<LL>(MT) == 0 && count_mode<LL>(MBR) == 0,
@@ -443,19 +443,21 @@ __global__ void __launch_bounds__(NTC + 32) k_bwd_bulk(const E e, const Slots sl
     const int nc = int(ce - c0 < CPS ? ce - c0 : CPS);
     if (nvalid > 0) {
       CT bpart[NB][V] = {};  // this stage's columns, summed plainly
-      for (int jc = 0; jc < nc; ++jc) {
-        Pack<LL, V, CT> p;
-        load_stage<LL, V, CT, TRB>(p, hold, smem + (st * CPS + jc) * SBC, sl, t, c0 + jc, nvalid);
-        GradAcc<LL, CT> g[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-#pragma unroll
-          for (int q = 0; q < NL; ++q) g[j].g[q] = grad_zero<CT>();
-          Ctx<LL, V, CT> cx{p, j};
-          e.bwd(cx, gL, g[j]);
+      // the host launches this kernel only for row counts that are a
+      // multiple of V, so every active thread takes the whole-vector body
+      auto columns = [&](auto full) {
+        constexpr bool F = decltype(full)::value;
+        for (int jc = 0; jc < nc; ++jc) {
+          Pack<LL, V, CT> p;
+          load_stage<LL, V, CT, TRB, F>(p, hold, smem + (st * CPS + jc) * SBC, sl, t, c0 + jc,
+                                        nvalid);
+          GradAcc<LL, CT, E> g[V];
+          grad_lanes<V>(e, p, gL, g);
+          bwd_store<LL, V, CT, NB, F>(g, bpart, ga, r, c0 + jc, R, nvalid);
         }
-        bwd_store<LL, V, CT, NB>(g, bpart, ga, r, c0 + jc, R, nvalid);
-      }
+      };
+      if (nvalid == V) columns(std::true_type{});
+      else columns(std::false_type{});
       if constexpr (NBC > 0) {
 #pragma unroll
         for (int b = 0; b < NB; ++b)

@@ -1006,10 +1006,67 @@ __global__ void __launch_bounds__(NT) k_row(const E e, const Slots sl, const int
 // for a = -0), so the compiler may drop the first add into each adjoint.
 template <class CT> FX_D CT grad_zero() { return -CT(0); }
 
-template <class LL, class CT> struct GradAcc {
+// Per-leaf adjoints of one element (or lane pair). A leaf that occurs once
+// in the tree E takes its adjoint by assignment (the add into -0 would be
+// exact too, but costs an instruction on lane pairs).
+template <class LL, class CT, class E> struct GradAcc {
   CT g[tl_size<LL>::value];
-  template <int K, int M> FX_D void add(CT a) { g[tl_index<LL, K, M>::value] += a; }
+  template <int K, int M> FX_D void add(CT a) {
+    constexpr int i = tl_index<LL, K, M>::value;
+    if constexpr (leaf_count<E, K, M>::value == 1) g[i] = a;
+    else g[i] += a;
+  }
 };
+
+// Pair context: lanes 2j and 2j + 1 of a pack as one F2.
+template <class LL, int V> struct Ctx2 {
+  using CT = F2;
+  const Pack<LL, V, float>& p;
+  int j;
+  template <int K, int M> FX_D F2 leaf() const {
+    constexpr int I = tl_index<LL, K, M>::value;
+    static_assert(I >= 0, "leaf not in the pack");
+    const auto& r = pget<I>::of(p);
+    if constexpr (M == MT) {
+      return F2(r.v[2 * j], r.v[2 * j + 1]);
+    } else if constexpr (M == MBR) {
+      const float x = to_compute<float>(r.v[0]);
+      return F2(x, x);
+    } else {
+      return F2(to_compute<float>(r.v[2 * j]), to_compute<float>(r.v[2 * j + 1]));
+    }
+  }
+};
+
+// Reverse pass of V lanes: every leaf's adjoint per lane. FP32 trees run
+// on lane pairs.
+template <int V, class E, class LL, class CT>
+FX_D void grad_lanes(const E& e, const Pack<LL, V, CT>& p, CT gL, GradAcc<LL, CT, E> (&g)[V]) {
+  constexpr int NL = tl_size<LL>::value;
+  if constexpr (std::is_same<CT, float>::value && V % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < V / 2; ++j) {
+      GradAcc<LL, F2, E> h;
+#pragma unroll
+      for (int q = 0; q < NL; ++q) h.g[q] = F2(-0.0f, -0.0f);
+      Ctx2<LL, V> cx{p, j};
+      e.bwd(cx, F2(gL, gL), h);
+#pragma unroll
+      for (int q = 0; q < NL; ++q) {
+        g[2 * j].g[q] = h.g[q].x;
+        g[2 * j + 1].g[q] = h.g[q].y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+#pragma unroll
+      for (int q = 0; q < NL; ++q) g[j].g[q] = grad_zero<CT>();
+      Ctx<LL, V, CT> cx{p, j};
+      e.bwd(cx, gL, g[j]);
+    }
+  }
+}
 
 struct GradArgs {
   void* g[FX_MAX_SLOTS];    // per input slot: dense column-major gradient, or null
@@ -1038,8 +1095,9 @@ template <class LL, int I, int J = 0> FX_HD constexpr int bc_rank() {
 // leaves' partial derivatives to per-row plain partial sums (the caller
 // folds those into the compensated running sums once per group of
 // columns: one compensated add per group instead of per element).
-template <class LL, int V, class CT, int NB, int I = 0>
-FX_D void bwd_store(const GradAcc<LL, CT> (&g)[V], CT (&bpart)[NB][V],
+// FULL: the caller knows that all V rows are inside the matrix.
+template <class LL, int V, class CT, int NB, bool FULL = false, int I = 0, class E>
+FX_D void bwd_store(const GradAcc<LL, CT, E> (&g)[V], CT (&bpart)[NB][V],
                     const GradArgs& ga, int64_t r, int64_t c, int64_t R, int nvalid) {
   if constexpr (I < tl_size<LL>::value) {
     using L = typename tl_at<LL, I>::type;
@@ -1048,7 +1106,7 @@ FX_D void bwd_store(const GradAcc<LL, CT> (&g)[V], CT (&bpart)[NB][V],
       T* dst = static_cast<T*>(ga.g[L::slot]);
       if (dst) {
         T* q = dst + r + c * R;  // dense, ld = R
-        if (nvalid == V) {
+        if (FULL || nvalid == V) {
           Raw<T, V> o;
 #pragma unroll
           for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(g[j].g[I]);
@@ -1063,9 +1121,9 @@ FX_D void bwd_store(const GradAcc<LL, CT> (&g)[V], CT (&bpart)[NB][V],
       constexpr int b = bc_rank<LL, I>();
 #pragma unroll
       for (int j = 0; j < V; ++j)
-        if (j < nvalid) bpart[b][j] += g[j].g[I];
+        if (FULL || j < nvalid) bpart[b][j] += g[j].g[I];
     }
-    bwd_store<LL, V, CT, NB, I + 1>(g, bpart, ga, r, c, R, nvalid);
+    bwd_store<LL, V, CT, NB, FULL, I + 1>(g, bpart, ga, r, c, R, nvalid);
   }
 }
 
@@ -1131,7 +1189,6 @@ __global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int
                                             const int64_t C, const GradArgs ga) {
   using LL = leaves_t<E>;
   using CT = ct_of<E>;
-  constexpr int NL = tl_size<LL>::value;
   constexpr int NBC = count_mode<LL>(MBC);
   static_assert(count_mode<LL>(MT) == 0 && count_mode<LL>(MBR) == 0,
                 "fused backward: plain and each_col leaves only");
@@ -1155,14 +1212,8 @@ __global__ void __launch_bounds__(NT) k_bwd(const E e, const Slots sl, const int
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (c + u < ce) {
-          GradAcc<LL, CT> g[V];
-#pragma unroll
-          for (int j = 0; j < V; ++j) {
-#pragma unroll
-            for (int k = 0; k < NL; ++k) g[j].g[k] = grad_zero<CT>();
-            Ctx<LL, V, CT> cx{p[u], j};
-            e.bwd(cx, gL, g[j]);
-          }
+          GradAcc<LL, CT, E> g[V];
+          grad_lanes<V>(e, p[u], gL, g);
           bwd_store<LL, V, CT, (NBC > 0 ? NBC : 1)>(g, bpart, ga, r, c + u, R, nvalid);
         }
       }

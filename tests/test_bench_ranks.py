@@ -113,3 +113,38 @@ def test_oracle_check_leg_on_cpu_tensors():
         assert d["max_scaled_err_sigma"] is not None and d["max_scaled_err_m"] is not None
     keep["colsum"][1][3] += 0.01 * float(keep["colsum"][1].abs().max())
     assert not bench.oracle_errors(keep, "f32", n_sample=512)["colsum"]["ok"]
+
+
+def test_oracle_check_leg_maps_suite_operands_to_slots():
+    """The Sec. 4 suite binds operands named A1.., P1, Y64 to trees whose
+    slots are X, Y, A, B ...: bench.oracle_errors must evaluate each tree on
+    its own slot names. Outputs made from the test harness's trees (typed
+    separately from the bench's) pass; a planted error in one fails."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import synth
+    from tests import harness
+    R = C = 40
+    env = synth.operands(4, [(f"A{k}", R, C) for k in range(1, 6)], "f32", "uniform")
+    env.update(synth.operands(5, [("P1", R, C), ("P2", R, C)], "f32", "positive"))
+    env.update(synth.operands(6, [("Y64", R, C)], "f64", "normal"))
+    trees = [("add5", "add5", [f"A{k}" for k in range(1, 6)]),
+             ("expr1", "expr1", ["A1", "A2"]), ("expr2", "expr2", ["A1", "A2", "A3", "A4"]),
+             ("expr3", "expr3", ["P1", "Y64", "P2"]), ("relu", "relu", ["A1"]),
+             ("sigmoid", "sigmoid", ["A1"]), ("swish", "swish", ["A1"]), ("gelu", "gelu", ["A1"])]
+    keep = {"env": env, "trees": []}
+    for name, key, ins in trees:
+        senv = {slot: env[i] for slot, i in zip(harness.SLOTS[name], ins)}
+        v = oracle.evaluate(harness.tree_of(name), senv)
+        keep[key] = (None, torch.from_numpy(v.T.ravel().astype(np.float32)))
+        keep["trees"].append((name, key, ins, "Z"))
+    errs = bench.oracle_errors(keep, "f32", n_sample=256)
+    assert set(errs) == {k for _, k, _ in trees}
+    for k, d in errs.items():
+        assert d["ok"], (k, d)
+    z = keep["gelu"][1]
+    z += 1e-3 * float(z.abs().max())
+    assert not bench.oracle_errors(keep, "f32", n_sample=256)["gelu"]["ok"]
