@@ -77,12 +77,43 @@ template <class LL, int V, class CTy> struct Ctx {
   }
 };
 
+// Pair context: lanes 2j and 2j + 1 of a pack as one F2.
+template <class LL, int V> struct Ctx2 {
+  using CT = F2;
+  const Pack<LL, V, float>& p;
+  int j;
+  template <int K, int M> FX_D F2 leaf() const {
+    constexpr int I = tl_index<LL, K, M>::value;
+    static_assert(I >= 0, "leaf not in the pack");
+    const auto& r = pget<I>::of(p);
+    if constexpr (M == MT) {
+      return F2(r.v[2 * j], r.v[2 * j + 1]);
+    } else if constexpr (M == MBR) {
+      const float x = to_compute<float>(r.v[0]);
+      return F2(x, x);
+    } else {
+      return F2(to_compute<float>(r.v[2 * j]), to_compute<float>(r.v[2 * j + 1]));
+    }
+  }
+};
+
+// The tree at V lanes of a pack; FP32 trees on lane pairs.
 template <int V, class E, class LL, class CT>
 FX_D void eval_lanes(const E& e, const Pack<LL, V, CT>& p, CT (&v)[V]) {
+  if constexpr (std::is_same<CT, float>::value && V % 2 == 0) {
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
-    Ctx<LL, V, CT> c{p, j};
-    v[j] = e.ev(c);
+    for (int j = 0; j < V / 2; ++j) {
+      Ctx2<LL, V> c{p, j};
+      const F2 w = e.ev(c);
+      v[2 * j] = w.x;
+      v[2 * j + 1] = w.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      Ctx<LL, V, CT> c{p, j};
+      v[j] = e.ev(c);
+    }
   }
 }
 
@@ -1015,26 +1046,6 @@ template <class LL, class CT, class E> struct GradAcc {
     constexpr int i = tl_index<LL, K, M>::value;
     if constexpr (leaf_count<E, K, M>::value == 1) g[i] = a;
     else g[i] += a;
-  }
-};
-
-// Pair context: lanes 2j and 2j + 1 of a pack as one F2.
-template <class LL, int V> struct Ctx2 {
-  using CT = F2;
-  const Pack<LL, V, float>& p;
-  int j;
-  template <int K, int M> FX_D F2 leaf() const {
-    constexpr int I = tl_index<LL, K, M>::value;
-    static_assert(I >= 0, "leaf not in the pack");
-    const auto& r = pget<I>::of(p);
-    if constexpr (M == MT) {
-      return F2(r.v[2 * j], r.v[2 * j + 1]);
-    } else if constexpr (M == MBR) {
-      const float x = to_compute<float>(r.v[0]);
-      return F2(x, x);
-    } else {
-      return F2(to_compute<float>(r.v[2 * j]), to_compute<float>(r.v[2 * j + 1]));
-    }
   }
 };
 
