@@ -173,7 +173,7 @@ FX_ADDN(16, "A1", "A2", "A3", "A4", "A5", "A6", "A7", "A8", "A9", "A10", "A11", 
 // expr1: Z = 2*(X.t() + Y) + 2*(X + Y.t()), X and Y square
 struct Expr1 {
   FX_DEF_COMMON("expr1", "(+ (* s0 (+ (t X) Y)) (* s0 (+ X (t Y))))", 2, 1, 1,
-                FX_KIND_ELEMENTWISE, dmask(FX_F32), false, false)
+                FX_KIND_ELEMENTWISE, ALL_DTYPES, false, false)
   static constexpr const char* slots[] = {"X", "Y", "Z"};
   static constexpr double defaults[] = {2.0};
   template <class T> static FX_HD auto build(const double* s) {

@@ -393,8 +393,10 @@ fx_status launch_tile_async(const Run& r, const E& e, const Slots& sl, int64_t R
 }
 
 // k_tile_tma: one CTA per SM (two with blocks_per_sm >= 2), as many
-// stages as fit next to the two output tiles. *used is false when the
-// operands are not TMA-addressable or fewer than two stages fit.
+// stages as fit next to the output tiles (two items' worth). Trees whose
+// TMA leaves are closed under transposition take symmetric tile pairs.
+// *used is false when the operands are not TMA-addressable or fewer than
+// two stages fit.
 template <class T, class E, class Epi>
 fx_status launch_tile_tma(const Run& r, const E& e, const Slots& sl, int64_t R, int64_t C,
                           const Epi& epi, RedArgs red, bool* used) {
@@ -411,7 +413,9 @@ fx_status launch_tile_tma(const Run& r, const E& e, const Slots& sl, int64_t R, 
     if constexpr (Epi::stores) {
       if (!encode_tile_map<T>(&tm.m[r.n_in], epi.z, R, C, epi.ldz)) return FX_OK;
     }
-    const int fixed = (Epi::stores ? 2 * G::LEAF : 0) + int(sizeof(Ring<kTmaMaxStages>)) + 1024;
+    constexpr bool SYM = flip_closed<LL>();
+    const int fixed = (Epi::stores ? 2 * (SYM ? 2 : 1) * G::LEAF : 0) +
+                      int(sizeof(Ring<kTmaMaxStages>)) + 1024;
     // Two CTAs per SM when two stages fit in half the shared memory (their
     // 16 consumer warps keep up with HBM on BF16 trees, where 8 do not),
     // else one; blocks_per_sm 1 or 2 forces the choice. 227 KB per SM,
@@ -424,7 +428,7 @@ fx_status launch_tile_tma(const Run& r, const E& e, const Slots& sl, int64_t R, 
     if (ns < 2 && r.tune.bps < 2) ns = stages(1);
     if (ns < 2) return FX_OK;
     const int smem = ns * SB + fixed;
-    auto kern = k_tile_tma<E, Epi, T, NTC>;
+    auto kern = k_tile_tma<E, Epi, T, NTC, SYM>;
     FX_TRY(allow_smem(kern, smem));
     unsigned int* err = nullptr;
     FX_TRY(err_word(r, &err));
@@ -434,7 +438,8 @@ fx_status launch_tile_tma(const Run& r, const E& e, const Slots& sl, int64_t R, 
       occ = 1;
     }
     const int sms = device_sms() > 0 ? device_sms() : 1;
-    const int64_t ntiles = ((R + G::TT - 1) / G::TT) * ((C + G::TT - 1) / G::TT);
+    const int64_t tr = (R + G::TT - 1) / G::TT;
+    const int64_t ntiles = SYM ? tr * (tr + 1) / 2 : tr * ((C + G::TT - 1) / G::TT);
     int64_t grid = int64_t(sms) * occ;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;

@@ -113,6 +113,33 @@ template <class LL, class T, int I = 0> FX_HD constexpr bool tma_uniform() {
   }
 }
 
+// Every TMA leaf (K, MN) has its transpose (K, MT) in the tree and the
+// other way round. Such a tree is square (leaf K is both R x C and C x R),
+// and the boxes loaded for output tile (i, j) are exactly those that tile
+// (j, i) needs, with the two modes of each leaf trading places.
+template <class LL, int I = 0> FX_HD constexpr bool flip_closed() {
+  if constexpr (I < tl_size<LL>::value) {
+    using L = typename tl_at<LL, I>::type;
+    constexpr bool ok = !(L::mode == MN || L::mode == MT) ||
+                        tl_index<LL, L::slot, flip_mode(L::mode)>::value >= 0;
+    return ok && flip_closed<LL, I + 1>();
+  } else {
+    return count_tma<LL>() > 0;
+  }
+}
+
+// Symmetric work items: tile pairs {(i, j), (j, i)} with i <= j, numbered
+// column by column (item q = j (j + 1) / 2 + i).
+FX_D void sym_pair(int64_t q, int64_t& i, int64_t& j) {
+  // FP32 estimate (FP64 is slow on this part), then exact integer fix-up
+  int64_t jj = int64_t((sqrtf(8.0f * float(q) + 1.0f) - 1.0f) * 0.5f);
+  if (jj < 0) jj = 0;
+  while ((jj + 1) * (jj + 2) / 2 <= q) ++jj;
+  while (jj * (jj + 1) / 2 > q) --jj;
+  j = jj;
+  i = q - jj * (jj + 1) / 2;
+}
+
 // Producer: the boxes of tile (r0, c0) of every TMA leaf into `stage`;
 // boxes that start outside the matrix are skipped. Returns the bytes issued.
 template <class LL, class T, int I = 0>
@@ -160,8 +187,10 @@ FX_D uint32_t tma_tile_bytes(int64_t R, int64_t C, int r0, int c0) {
   return uint32_t(count_mode<LL>(MN) * nr + count_mode<LL>(MT) * nc) * uint32_t(G::BOX);
 }
 
-// Consumer: rows r..r+V-1 of tile column c of every leaf.
-template <class LL, class T, class CT, int I = 0>
+// Consumer: rows r..r+V-1 of tile column c of every leaf. SWAP: the stage
+// holds the boxes of the transposed tile, so each TMA leaf reads the region
+// its flipped twin was loaded into.
+template <class LL, class T, class CT, bool SWAP = false, int I = 0>
 FX_D void load_tma_pack(Pack<LL, TmaGeom<T>::V, CT>& p, const char* stage, const Slots& sl,
                         int64_t r0, int64_t c0, int r, int c, int nvalid) {
   using G = TmaGeom<T>;
@@ -170,7 +199,10 @@ FX_D void load_tma_pack(Pack<LL, TmaGeom<T>::V, CT>& p, const char* stage, const
     using L = typename tl_at<LL, I>::type;
     using TL_ = typename L::elem;
     auto& dst = pget<I>::of(p);
-    const char* base = stage + tma_rank<LL, I>() * G::LEAF;
+    constexpr int J = (SWAP && (L::mode == MN || L::mode == MT))
+                          ? tl_index<LL, L::slot, flip_mode(L::mode)>::value
+                          : I;
+    const char* base = stage + tma_rank<LL, J>() * G::LEAF;
     if constexpr (L::mode == MN) {
       const char* q = base + (r / G::IB) * G::BOX + swz<G::es>(r % G::IB, c);
       dst = *reinterpret_cast<const Raw<T, V>*>(q);
@@ -189,13 +221,16 @@ FX_D void load_tma_pack(Pack<LL, TmaGeom<T>::V, CT>& p, const char* stage, const
       const SlotView& s = sl.s[L::slot];
       dst.v[0] = sload(static_cast<const TL_*>(s.p) + (c0 + c) * s.vs);
     }
-    load_tma_pack<LL, T, CT, I + 1>(p, stage, sl, r0, c0, r, c, nvalid);
+    load_tma_pack<LL, T, CT, SWAP, I + 1>(p, stage, sl, r0, c0, r, c, nvalid);
   }
 }
 
 constexpr int kTmaMaxStages = 8;
 
-template <class E, class Epi, class T, int NTC>
+// SYM (trees whose TMA leaves are closed under transposition): one work
+// item is the tile pair {(i, j), (j, i)}, loaded once and evaluated twice,
+// so each input element is read once instead of twice.
+template <class E, class Epi, class T, int NTC, bool SYM = false>
 __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl, const int64_t R,
                                                         const int64_t C, const Epi epi,
                                                         const RedArgs red,
@@ -209,17 +244,24 @@ __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl
   constexpr int SB = count_tma<LL>() * G::LEAF;       // one stage
   constexpr int NPT = (TT / V) * TT / NTC;             // vectors per thread per tile
   static_assert(NPT * NTC == (TT / V) * TT, "tile / thread shape");
+  static_assert(!SYM || flip_closed<LL>(), "symmetric items need a transpose-closed tree");
   constexpr bool ST = Epi::stores;
+  constexpr int ZT = SYM ? 2 : 1;                      // output tiles per item
   extern __shared__ char smem_raw[];
   char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  char* zbuf = smem + ns * SB;                         // two output tiles when storing
+  char* zbuf = smem + ns * SB;                         // two items' output tiles when storing
   Ring<kTmaMaxStages>& ring =
-      *reinterpret_cast<Ring<kTmaMaxStages>*>(zbuf + (ST ? 2 * G::LEAF : 0));
+      *reinterpret_cast<Ring<kTmaMaxStages>*>(zbuf + (ST ? 2 * ZT * G::LEAF : 0));
   const int64_t tiles_r = (R + TT - 1) / TT, tiles_c = (C + TT - 1) / TT;
-  const int64_t ntiles = tiles_r * tiles_c;
+  const int64_t nitems = SYM ? tiles_r * (tiles_r + 1) / 2 : tiles_r * tiles_c;
   const int64_t G_ = gridDim.x;
-  const int64_t mine = ntiles > int64_t(blockIdx.x) ? (ntiles - blockIdx.x + G_ - 1) / G_ : 0;
+  const int64_t mine = nitems > int64_t(blockIdx.x) ? (nitems - blockIdx.x + G_ - 1) / G_ : 0;
   const int tid = threadIdx.x;
+  // output tile of item t: (tr, tc), and for SYM also (tc, tr) when tr != tc
+  auto coords = [&](int64_t t, int64_t& tr, int64_t& tc) {
+    if constexpr (SYM) sym_pair(t, tr, tc);
+    else tile_coords(t, tiles_r, tiles_c, tr, tc);
+  };
   if (tid == 0) {
     for (int i = 0; i < ns; ++i) {
       tma::mbar_init(&ring.full[i], 1);
@@ -243,7 +285,7 @@ __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl
           break;
         }
         int64_t tr, tc;
-        tile_coords(blockIdx.x + k * G_, tiles_r, tiles_c, tr, tc);
+        coords(blockIdx.x + k * G_, tr, tc);
         const int r0 = int(tr * TT), c0 = int(tc * TT);
         tma::arrive_expect_tx(&ring.full[s], tma_tile_bytes<LL, T>(R, C, r0, c0));
         issue_tma_tile<LL, T>(smem + s * SB, maps, R, C, r0, c0, &ring.full[s]);
@@ -254,26 +296,16 @@ __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl
       }
     }
   } else {
-    for (int64_t k = 0; k < mine; ++k) {
-      const int s = int(k % ns);
-      if (!tma::wait(&ring.full[s], uint32_t((k / ns) & 1), err)) ring.abort = 1;
-      if constexpr (ST) {
-        if (tid == 0 && k >= 2) tma::store_wait_read<1>();  // output tile k-2 read out
-      }
-      block_sync(NTC);
-      if (ring.abort) break;  // uniform: set only before this barrier
-      int64_t tr, tc;
-      tile_coords(blockIdx.x + k * G_, tiles_r, tiles_c, tr, tc);
-      const int64_t r0 = tr * TT, c0 = tc * TT;
-      const char* stage = smem + s * SB;
-      char* zt = zbuf + int(k & 1) * G::LEAF;
+    // one output tile at (r0, c0) from the stage; SWAP reads the transposed tile's boxes
+    auto tile = [&](const char* stage, int64_t r0, int64_t c0, char* zt, auto swap) {
+      constexpr bool SW = decltype(swap)::value;
 #pragma unroll
       for (int q = 0; q < NPT; ++q) {
         const int vi = tid + q * NTC;
         const int c = vi % TT, r = (vi / TT) * V;
         const int nvalid = (c0 + c < C) ? clamp_valid(R - r0 - r, V) : 0;
         Pack<LL, V, CT> p;
-        load_tma_pack<LL, T, CT>(p, stage, sl, r0, c0, r, c, nvalid);
+        load_tma_pack<LL, T, CT, SW>(p, stage, sl, r0, c0, r, c, nvalid);
         CT v[V];
         eval_lanes<V>(e, p, v);
         if constexpr (ST) {
@@ -297,15 +329,37 @@ __global__ void __launch_bounds__(NTC + 32) k_tile_tma(const E e, const Slots sl
           }
         }
       }
+    };
+    auto store_tile = [&](int64_t r0, int64_t c0, const char* zt) {
+#pragma unroll
+      for (int b = 0; b < G::NB; ++b)
+        if (r0 + b * G::IB < R) tma::store_2d(&maps.m[zslot], int(r0) + b * G::IB, int(c0), zt + b * G::BOX);
+    };
+    for (int64_t k = 0; k < mine; ++k) {
+      const int s = int(k % ns);
+      if (!tma::wait(&ring.full[s], uint32_t((k / ns) & 1), err)) ring.abort = 1;
+      if constexpr (ST) {
+        if (tid == 0 && k >= 2) tma::store_wait_read<1>();  // output tiles of item k-2 read out
+      }
+      block_sync(NTC);
+      if (ring.abort) break;  // uniform: set only before this barrier
+      int64_t tr, tc;
+      coords(blockIdx.x + k * G_, tr, tc);
+      const int64_t r0 = tr * TT, c0 = tc * TT;
+      const char* stage = smem + s * SB;
+      char* zt = zbuf + int(k & 1) * ZT * G::LEAF;
+      tile(stage, r0, c0, zt, std::false_type{});
+      const bool second = SYM && tr != tc;
+      if constexpr (SYM) {
+        if (second) tile(stage, c0, r0, zt + G::LEAF, std::true_type{});
+      }
       tma::arrive(&ring.empty[s]);
       if constexpr (ST) {
         tma::fence_proxy_async();  // this thread's output writes, visible to the TMA store
         block_sync(NTC);
         if (tid == 0) {
-#pragma unroll
-          for (int b = 0; b < G::NB; ++b)
-            if (r0 + b * G::IB < R)
-              tma::store_2d(&maps.m[zslot], int(r0) + b * G::IB, int(c0), zt + b * G::BOX);
+          store_tile(r0, c0, zt);
+          if (second) store_tile(c0, r0, zt + G::LEAF);
           tma::store_commit();
         }
       }

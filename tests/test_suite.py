@@ -63,6 +63,26 @@ def test_suite_expressions(fx, name):
         check(name, got, env, f" at {R}x{C}")
 
 
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16"])
+def test_expr1_symmetric_tile_pairs(fx, storage):
+    """expr1 reads X and Y both plain and transposed, so on the TMA kernel
+    (launch-shape pipeline 0) one work item is the tile pair {(i, j), (j, i)}:
+    the four boxes are loaded once and both output tiles are written. Square
+    sizes from one tile to many, with and without a ragged last tile (64 and
+    32 elements per tile side), a padded output, one and two CTAs per SM;
+    every element against the oracle."""
+    for n in [8, 64, 72, 136, 1000]:
+        env = synth.operands(70 + n, specs_for("expr1", n, n), storage, "normal")
+        for shape, ldz in [((256, 4, 0, 0), None), ((256, 4, 1, 0), n + 8), ((256, 4, 2, 0), None)]:
+            got = run(fx, "expr1", storage, env, n, n, shape=shape, ldz=ldz)
+            for key, (rv, rs) in oracle_outputs("expr1", env).items():
+                tol = tolerance("expr1", storage, key)
+                err, _, bad, _ = scaled_error(got[key], rv, rs, storage)
+                assert bad == 0, f"expr1 {storage} {n}^2 {shape}: {bad} wrong non-finite outputs"
+                assert err <= tol, f"expr1 {storage} {n}^2 {shape}: {err:.3e} > {tol:.1e}"
+            assert got["_launches"] == 1
+
+
 def expr3_env(seed, R, C):
     """expr3's inputs: X and W positive FP32 (the logs stay defined), Y FP64."""
     env = synth.operands(seed, [("X", R, C), ("W", R, C)], "f32", "positive")
