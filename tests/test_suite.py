@@ -83,6 +83,20 @@ def test_expr1_symmetric_tile_pairs(fx, storage):
             assert got["_launches"] == 1
 
 
+@pytest.mark.parametrize("name", ["add5", "sum_schur", "relu"])
+def test_lane_pairs_round_like_scalar_lanes(fx, name):
+    """FP32 trees run on lane pairs (add/sub/mul.rn.f32x2) when their
+    operands are 16-byte aligned and lane by lane when they are not (inputs
+    one element off alignment take the one-lane path). Trees of adds and
+    multiplies only, with no product added to something (where the two
+    paths may contract differently), must agree bit for bit."""
+    for R, C in [(333, 129), (64, 64), (1000, 7)]:
+        env = synth.operands(80, specs_for(name, R, C), "f32", "normal")
+        paired = run(fx, name, "f32", env, R, C)
+        single = run(fx, name, "f32", env, R, C, offset=1)
+        assert np.array_equal(paired["Z"], single["Z"]), f"{name} at {R}x{C}"
+
+
 def expr3_env(seed, R, C):
     """expr3's inputs: X and W positive FP32 (the logs stay defined), Y FP64."""
     env = synth.operands(seed, [("X", R, C), ("W", R, C)], "f32", "positive")
