@@ -183,13 +183,15 @@ class Clocks:
 # ---------------------------------------------------------------- workloads
 
 class Op:
-    """One fused evaluation: a launch, its unfused twin, its algorithmic bytes
-    and (trees with a matrix product) its algorithmic flops."""
+    """One fused evaluation: a launch, its unfused twin, its algorithmic bytes,
+    its elements (output elements, or the elements a reduction reduces) and
+    (trees with a matrix product) its algorithmic flops."""
 
-    def __init__(self, key, nbytes, launch, unfused=None, launches=None, flops=0):
+    def __init__(self, key, nbytes, launch, unfused=None, launches=None, flops=0, elems=0):
         self.key, self.bytes, self.launch, self.unfused, self.launches = (
             key, nbytes, launch, unfused, launches)
         self.flops = flops
+        self.elems = elems
 
 
 def _bind(fx, h, k, t, rows, cols, ld):
@@ -253,7 +255,7 @@ def _expr_ops(fx, torch, dev, sp, trees, storage, env, R, C, keep, check=True):
             keep.setdefault("trees", []).append((name, key, list(ins), kind))
         ops.append(Op(key, nb, (lambda h=h: fx.fx_eval(h, sp)),
                       (lambda h=h: fx.fx_eval_unfused(h, sp)),
-                      (lambda h=h: fx.fx_expr_last_launches(h))))
+                      (lambda h=h: fx.fx_expr_last_launches(h)), elems=R * C))
     return ops
 
 
@@ -372,7 +374,8 @@ def gemm_workload(fx, torch, dev, sp, keep, storage, size=8192):
                 keep.setdefault("gemm_checks", []).append((name, key, ins, scal))
             ops.append(Op(key + suffix, nb, (lambda h=h: fx.fx_eval(h, sp)),
                           (lambda h=h: fx.fx_eval_unfused(h, sp)),
-                          (lambda h=h: fx.fx_expr_last_launches(h)), flops=flops))
+                          (lambda h=h: fx.fx_expr_last_launches(h)), flops=flops,
+                          elems=M * N))
         return ops
 
     ops = make(0, "", True)
@@ -453,7 +456,7 @@ def batch_workload(fx, torch, dev, sp, keep, count=4096):
             fx.fx_eval_unfused(e, sp)
 
     op = Op("batch", nbytes, lambda: fx.fx_eval_batch(h, items, sp, True), unfused,
-            lambda: fx.fx_expr_last_launches(h))
+            lambda: fx.fx_expr_last_launches(h), elems=nel)
     cfg = {"workload": f"Z=A%B+0.5*trans(C), s=accu(Z) over {n} matrices, rows/cols "
                        "log-uniform [16,2048] seed 2", "matrices": n, "elements": nel,
            "l2": "working set 11.5 GB, no flush", "graph": True}
@@ -489,9 +492,9 @@ def loss_workload(fx, torch, dev, sp, keep, storage, size=8192):
     fwd_bytes = 3 * R * C * es + R * es + 4
     bwd_bytes = 3 * R * C * es + R * es + 2 * R * C * es + R * es
     ops = [Op("forward", fwd_bytes, lambda: fx.fx_eval(h, sp), lambda: fx.fx_eval_unfused(h, sp),
-              lambda: fx.fx_expr_last_launches(h)),
+              lambda: fx.fx_expr_last_launches(h), elems=R * C),
            Op("backward", bwd_bytes, lambda: fx.fx_eval_backward(h, 0, ptrs, sp), None,
-              lambda: fx.fx_expr_last_launches(h))]
+              lambda: fx.fx_expr_last_launches(h), elems=R * C)]
     cfg = {"workload": f"L=accu(square(sigmoid(X%W+b.each_col)-Y)) forward and backward (dX,dW,db), "
                        f"{R}x{C} {storage}", "rows": R, "cols": C,
            "inputs": "X,W,Y,b N(0, sd 0.5), seed 3", "l2": "inputs larger than L2, no flush"}
@@ -957,6 +960,7 @@ def run_config(args, name, fx, torch, dev, stream, sp, peak, K, W):
                          "avg_launch_ms": round(per_ms[dom], 4)},
             "per_op": {k: {"ms": round(per_ms[k], 4), "bytes": next(o.bytes for o in ops if o.key == k),
                            "gbs": round(next(o.bytes for o in ops if o.key == k) / per_ms[k] / 1e6, 1),
+                           "gelems_per_s": round(next(o.elems for o in ops if o.key == k) / per_ms[k] / 1e6, 2),
                            "unfused_ms": round(u_ms[k], 4) if k in u_ms else None}
                        for k in per_ms},
             "gpu_launches": launches, "launch_shape": cfg.get("launch_shape"), "l2": cfg["l2"],
@@ -1077,6 +1081,7 @@ def run_ours(args, rank, world):
                        "min_ms": round(min(per_all[k]), 4),
                        "bytes": next(o.bytes for o in ops if o.key == k),
                        "gbs": round(next(o.bytes for o in ops if o.key == k) / per_ms[k] / 1e6, 1),
+                       "gelems_per_s": round(next(o.elems for o in ops if o.key == k) / per_ms[k] / 1e6, 2),
                        "unfused_ms": round(u_ms[k], 4) if k in u_ms else None}
                    for k in per_ms},
         "roofline": {"bound": "hbm", "achieved": round(z_gbs, 2), "peak": peak,
