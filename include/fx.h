@@ -214,7 +214,9 @@ fx_status fx_tune(fx_expr* x, fx_tune_mode mode, void* stream);
 /* Autotuner of the batched entry (fx_eval_batch): times the batched
  * kernel's launch shapes - threads per block 256 or 512 (512 not for BF16 /
  * FP16), 2, 3 or 4 pipeline stages (reported as unroll 2, 4, 8), blocks per
- * SM 0 (as many as fit), 1 or 2 - on the given items without graph capture,
+ * SM 0 (as many as fit), 1 or 2, and the vector width each thread
+ * evaluates per step (reported as pipeline 0: 16 bytes of elements, 1: 8
+ * bytes) - on the given items without graph capture,
  * keeps the fastest and caches it under (expression, storage, device, n).
  * FX_TUNE_CACHE reads the cache; FX_TUNE_OFF restores the defaults. The
  * next fx_eval_batch uses the chosen shape (and re-captures its graph). */

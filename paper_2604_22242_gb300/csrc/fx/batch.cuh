@@ -248,20 +248,25 @@ template <class RT> FX_D double2 load_partial(const double2* part, int64_t i) {
   }
 }
 
-template <class E, class T, int TR, int TC, int NT, int NBUF, int KIND, int NIN>
+// VC: consecutive slots of one column a thread evaluates per step (its
+// vector width: 16 bytes of elements, or half that); copies and skews stay
+// in 16-byte chunks of W elements.
+template <class E, class T, int TR, int TC, int NT, int NBUF, int KIND, int NIN, int VC>
 __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* __restrict__ mats,
                                                     const BatchItem* __restrict__ items,
                                                     const int64_t nitems, double2* part) {
   using LL = leaves_t<E>;
   using CT = ct_of<E>;
   constexpr int AB = abuf_bytes<LL, TR, TC>();
-  constexpr int V = 16 / int(sizeof(T));  // also the largest row skew + 1
+  constexpr int W = 16 / int(sizeof(T));  // elements of a 16-byte chunk; the largest row skew + 1
+  constexpr int V = VC;
+  static_assert(V >= 1 && W % V == 0, "vector width divides the chunk");
   extern __shared__ __align__(128) char smem[];
   TileDesc* desc = reinterpret_cast<TileDesc*>(smem + NBUF * AB);
   const int64_t G = gridDim.x;
   const int64_t mine = nitems > int64_t(blockIdx.x) ? (nitems - blockIdx.x + G - 1) / G : 0;
   auto fetch = [&](int64_t j) {
-    return fetch_item<NIN, TR, TC, KIND, V>(mats, items, blockIdx.x + j * G, j < mine);
+    return fetch_item<NIN, TR, TC, KIND, W>(mats, items, blockIdx.x + j * G, j < mine);
   };
   // issue a fetched item into buffer b (every thread commits a group, even an empty one)
   auto issue = [&](const IssueDesc<NIN>& d, int b) {
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
 #pragma unroll
     for (int c = threadIdx.x / RG; c < TC; c += NT / RG) {
       if (c < cc) {
-        const int sk = col_skew<V>(d.sld, d.sbase, c0 + c);
+        const int sk = col_skew<W>(d.sld, d.sbase, c0 + c);
         const int row = r0 - sk + i;  // output row of slot i
         Pack<LL, V, CT> p;
         CT v[V];
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(NT) k_batch_async(const E e, const BatchMat* _
           eval_lanes<V>(e, p, v);
           if constexpr (KIND != FX_KIND_FULL_REDUCE) {
             T* q = z + (row + c * ldz);
-            if ((reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+            if ((reinterpret_cast<uintptr_t>(q) & uintptr_t(V * sizeof(T) - 1)) == 0) {
               Raw<T, V> o;
 #pragma unroll
               for (int j = 0; j < V; ++j) o.v[j] = narrow_to<T>::from(v[j]);
@@ -397,7 +402,7 @@ struct BatchCacheEntry {
   double2* part = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t exec_stream = nullptr;
-  int exec_shape[3] = {0, 0, 0};  // launch shape the graph was captured with
+  int exec_shape[4] = {0, 0, 0, 0};  // launch shape the graph was captured with
 };
 
 }  // namespace fx
@@ -625,13 +630,17 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
     Run r = run_of(x, st);
     // Launch shape (tunable, fx_tune_batch): threads per block 256 or 512
     // (512 not for 2-byte types), 2, 3 or 4 pipeline stages (unroll 2, 4,
-    // 8), blocks per SM (0: as many as fit).
+    // 8), blocks per SM (0: as many as fit), and the vector width a thread
+    // evaluates per step (pipeline 1: 8 bytes of elements; otherwise 16).
     const int NTsel = (r.tune.block >= 512 && sizeof(T) != 2) ? 512 : 256;
     const int NBsel = r.tune.unroll <= 2 ? 2 : (r.tune.unroll >= 8 ? 4 : 3);
+    const int VHsel = r.tune.pipe == 1 ? 1 : 0;
+    constexpr int VW = 16 / int(sizeof(T));
     auto launch_one = [&](auto nt_c, auto nb_c) -> fx_status {
       constexpr int NT = decltype(nt_c)::value, NBUF = decltype(nb_c)::value;
       constexpr int KE = kind == FX_KIND_MULTI ? FX_KIND_MULTI : KIND0;
-      auto kern = k_batch_async<E, T, TR, TCc, NT, NBUF, KE, NIN>;
+      auto kern = VHsel ? k_batch_async<E, T, TR, TCc, NT, NBUF, KE, NIN, VW / 2>
+                        : k_batch_async<E, T, TR, TCc, NT, NBUF, KE, NIN, VW>;
       constexpr int smem = NBUF * abuf_bytes<LL, TR, TCc>() + NBUF * int(sizeof(TileDesc));
       FX_TRY(allow_smem(kern, smem));
       const int sms = device_sms() > 0 ? device_sms() : 1;
@@ -671,7 +680,7 @@ fx_status run_batch(fx_expr* x, const Root& root, int64_t n, const fx_batch_item
       return FX_OK;
     };
     if (!use_graph || st == nullptr) return launch_all();
-    const int shape[3] = {NTsel, NBsel, r.tune.bps};
+    const int shape[4] = {NTsel, NBsel, r.tune.bps, VHsel};
     if (!c.exec || c.exec_stream != st || memcmp(shape, c.exec_shape, sizeof shape) != 0) {
       if (c.exec) {
         cudaGraphExecDestroy(c.exec);

@@ -112,8 +112,9 @@ template <class LL, bool ALL_MIXED = false> struct SlotModes {
 };
 
 // Batch autotuner: the same search over the batched kernel's launch shapes
-// (threads per block 256 / 512, 2 / 3 / 4 stages, blocks per SM), timed on
-// the given items without graph capture; cached under the batch size.
+// (threads per block 256 / 512, 2 / 3 / 4 stages, blocks per SM, vector
+// width 16 or 8 bytes as pipeline 0 or 1), timed on the given items without
+// graph capture; cached under the batch size.
 using BatchRunFn = fx_status (*)(fx_expr*, int64_t, const fx_batch_item*, cudaStream_t, int);
 inline fx_status run_tune_batch(fx_expr* x, int mode, cudaStream_t st, int64_t n,
                                 const fx_batch_item* items, BatchRunFn run) {
@@ -126,16 +127,18 @@ inline fx_status run_tune_batch(fx_expr* x, int mode, cudaStream_t st, int64_t n
   static const int blocks[] = {256, 512};
   static const int unrolls[] = {2, 4, 8};
   static const int bpss[] = {0, 1, 2};
+  static const int widths[] = {0, 1};
   cudaEvent_t a, b;
   FX_CUDA(cudaEventCreate(&a));
   FX_CUDA(cudaEventCreate(&b));
   Tune best{};
   float best_ms = 1e30f;
   fx_status status = FX_OK;
+  for (int vw : widths)
   for (int bl : blocks)
     for (int un : unrolls)
       for (int bp : bpss) {
-        x->tune = Tune{bl, un, bp, true, 0};
+        x->tune = Tune{bl, un, bp, true, vw};
         for (int w = 0; w < 2 && status == FX_OK; ++w) status = run(x, n, items, st, 0);
         if (status != FX_OK) break;
         cudaEventRecord(a, st);

@@ -27,7 +27,8 @@ struct Tune {
   int bps = 0;
   bool tuned = false;
   // kernel variant: 0 the library's choice per tree, 1 copy pipelines
-  // (cp.async tiles, bulk-copy flat chunks and rows), 2 register loads
+  // (cp.async tiles, bulk-copy flat chunks and rows), 2 register loads; for
+  // the batched kernel, 1 selects 8-byte vectors per thread instead of 16
   int pipe = 0;
 };
 

@@ -136,10 +136,12 @@ def test_batch_4096_log_uniform(fx):
     assert np.all(np.isfinite(ss))
 
 
-@pytest.mark.parametrize("shape", [(512, 2, 0, 0), (256, 8, 1, 0), (512, 4, 2, 0), (256, 2, 0, 0)])
+@pytest.mark.parametrize("shape", [(512, 2, 0, 0), (256, 8, 1, 0), (512, 4, 2, 0), (256, 2, 0, 0),
+                                   (256, 4, 0, 1), (512, 2, 2, 1), (256, 8, 0, 1)])
 def test_batch_launch_shapes(fx, shape):
     """Every batched launch shape the tuner picks from: 256/512 threads,
-    2/3/4 stages, residency; direct and graph-captured."""
+    2/3/4 stages, residency, 16- or 8-byte vectors per thread (pipeline 0 /
+    1); direct and graph-captured."""
     rows, cols, ops = synth.batch_operands(7, 50, [("A", False), ("B", False), ("C", True)],
                                            lo=1, hi=260)
     for use_graph in (False, True):
@@ -155,7 +157,60 @@ def test_batch_autotune(fx, tmp_path, monkeypatch):
     zs, ss, _ = run_batch(fx, rows, cols, ops, True, tune="search", shape_out=got)
     check(ops, rows, cols, zs, ss, range(len(rows)))
     b, u, s, p = got[0]
-    assert b in (256, 512) and u in (2, 4, 8) and s in (0, 1, 2)
+    assert b in (256, 512) and u in (2, 4, 8) and s in (0, 1, 2) and p in (0, 1)
     again = []
     run_batch(fx, rows, cols, ops, True, tune="cache", shape_out=again)
     assert again[0] == got[0]
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+@pytest.mark.parametrize("shape", [(256, 2, 0, 0), (256, 4, 0, 1)])
+def test_batch_other_storage_types(fx, storage, shape):
+    """The batched kernel in FP64 (32-row tiles, 2-element chunks) and BF16
+    (8-element chunks) storage, at both vector widths (pipeline 0: 16 bytes
+    per thread per step, 1: 8 bytes); every matrix against the oracle at the
+    storage type's tolerance."""
+    import torch
+
+    from harness import STORAGE_CODE, from_device, oracle_outputs, to_device, tolerance
+    from oracle.compare import ErrorReport
+    rows, cols, ops = synth.batch_operands(9, 24, [("A", False), ("B", False), ("C", True)],
+                                           lo=1, hi=150, storage=storage)
+    n = len(rows)
+    tdt = torch.float64 if storage == "f64" else torch.bfloat16
+    rdt = torch.float64 if storage == "f64" else torch.float32
+    dev = {k: [to_device(ops[k][i]) for i in range(n)] for k in "ABC"}
+    zs = [torch.full((max(int(r) * int(c), 1),), float("nan"), dtype=tdt, device="cuda")
+          for r, c in zip(rows, cols)]
+    S = torch.full((n,), float("nan"), dtype=rdt, device="cuda")
+    items = (fx.BatchItem * n)()
+    for i in range(n):
+        it = items[i]
+        for k, name in enumerate("ABC"):
+            it.ptr[k] = dev[name][i].data_ptr()
+        it.ptr[3] = zs[i].data_ptr()
+        it.ptr[4] = S.data_ptr() + i * S.element_size()
+        it.rows, it.cols = int(rows[i]), int(cols[i])
+    h = fx.fx_expr_create("schur_trans_accu", STORAGE_CODE[storage])
+    try:
+        fx.fx_expr_set_launch_shape(h, *shape)
+        for use_graph in (False, True):
+            fx.fx_eval_batch(h, items, 0, use_graph)
+            torch.cuda.synchronize()
+            s_got = S.cpu().numpy().astype(np.float64)
+            for i in range(n):
+                r, c = int(rows[i]), int(cols[i])
+                env = {k: ops[k][i] for k in "ABC"}
+                ref = oracle_outputs("schur_trans_accu", env)
+                z = from_device(zs[i][: r * c], storage).reshape(c, r).T if r * c else np.zeros((r, c))
+                zr, zm = ref["Z"]
+                tz = tolerance("schur_trans_accu", storage, "Z")
+                rz = ErrorReport(storage, tz, "m").add(z, zr, mag=zm)
+                assert rz.nonfinite == 0 and rz.err <= tz, (storage, shape, i, r, c, rz.err)
+                v, sv = ref["s"]
+                ts = tolerance("schur_trans_accu", storage, "s")
+                rs = ErrorReport("f64" if storage == "f64" else "f32", ts, "m").add(
+                    [s_got[i]], [v], mag=[sv])
+                assert rs.nonfinite == 0 and rs.err <= ts, (storage, shape, i, "s", rs.err)
+    finally:
+        fx.fx_expr_destroy(h)
