@@ -66,7 +66,7 @@ METRIC = "fused-expr effective HBM GB/s (% of GB300 peak) and speedup vs unfused
 # valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the first
-    # timed launch of Z at 8192^2 FP32 (profiles/k_flat_schur_sqrt_sigmoid_f32.md),
+    # timed launch of Z at 8192^2 FP32 (the flat kernel's summary under profiles/),
     # read + write per (threads per block, vectors per leaf) of the register
     # kernel k_flat, every shape the autotuner searches (pipelines 0 and 2 of
     # this four-leaf tree; the blocks-per-SM cap only changes the grid of the
